@@ -1,0 +1,156 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle runs.
+
+This module holds parameter records and random-field generators only: no step
+of the lattice Boltzmann method is computed here.  Both the CUDA library and
+the CPU oracle receive exactly the arrays it returns.
+
+Workloads (the five configurations the library is measured and checked on):
+  c1  D1Q3, 2 components, 256 periodic nodes, FP64: symmetric mixture, slab
+  c2  D2Q9, 2 components, 1024 x 1024, FP64 and FP32-mixed: spinodal decomposition
+  c3  batched sweep of independent D1Q3 and D2Q9 runs (FP32-mixed)
+  c4  D2Q9, 4 components, 2048 x 2048, FP32-mixed: random symmetric mixture
+  c5  D2Q9, 2 components, 512 x 512: adjoint rollout (config-2 mixture, a12 = 0.75)
+Seeds: configuration k draws from numpy ``default_rng(1805072510 + k)``; run r
+of the sweep from ``default_rng(1805072600 + r)``.
+
+Readings fixed here (each is stated with its reason in the design notes):
+  * kT is a fraction of the van der Waals one-fluid critical temperature at the
+    run's mean mole fractions x: theta_cr^mix = 8 (x.a.x) / (27 b.x), the
+    single-component relation theta_cr = 8a/(27b) of Sec. II with a and b
+    replaced by their quadratic and linear mole-fraction averages.
+  * kappa^{cc'} = kappa for every pair; lambda^{cc'} = 1 between different
+    components (the paper gives no lambda; equilibrium does not depend on it).
+  * gamma_mu and the slab width come from ``params.json``, written by
+    ``tests/golden/make_config_params.py`` from the oracle (Sec. V rule
+    c_s^2 = 1 - 4 kappa rho_l gamma_mu, then a stability pre-scan).
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+
+SEED_BASE = 1805072510
+SWEEP_SEED_BASE = 1805072600
+_HERE = os.path.dirname(os.path.abspath(__file__))
+PARAMS_JSON = os.path.join(_HERE, "params.json")
+
+
+def seed(k):
+    return SEED_BASE + int(k)
+
+
+def rng(k):
+    return np.random.default_rng(seed(k))
+
+
+def one_fluid_critical_kT(a, b, x):
+    """van der Waals one-fluid critical temperature 8 (x.a.x) / (27 b.x)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    return 8.0 * float(x @ a @ x) / (27.0 * float(b @ x))
+
+
+def _stored():
+    if os.path.exists(PARAMS_JSON):
+        with open(PARAMS_JSON) as fh:
+            return json.load(fh)
+    return {}
+
+
+def _offdiag(N, v):
+    m = np.full((N, N), float(v))
+    np.fill_diagonal(m, 0.0)
+    return m
+
+
+def base_params(name):
+    """Parameter record (dict) of workload ``name`` without its fields."""
+    st = _stored().get(name, {})
+    if name == "c1":
+        a = np.array([[1.0, 0.7], [0.7, 1.0]])
+        b = np.array([0.25, 0.25])
+        x = np.array([0.5, 0.5])
+        p = dict(lattice="D1Q3", nx=256, ny=1, ncomp=2, tau=1.0, a=a, b=b,
+                 kappa=np.full((2, 2), 0.1), lam=_offdiag(2, 1.0),
+                 kT=0.9 * one_fluid_critical_kT(a, b, x), steps=10000, x=x)
+    elif name in ("c2", "c5"):
+        a12 = 0.9 if name == "c2" else 0.75
+        a = np.array([[1.0, a12], [a12, 0.6]])
+        b = np.array([0.25, 0.3])
+        x = np.array([0.4, 0.6])
+        n = 1024 if name == "c2" else 512
+        p = dict(lattice="D2Q9", nx=n, ny=n, ncomp=2, tau=1.0, a=a, b=b,
+                 kappa=np.full((2, 2), 0.1), lam=_offdiag(2, 1.0),
+                 kT=0.85 * one_fluid_critical_kT(a, b, x),
+                 steps=10000 if name == "c2" else 2000, x=x, rho_total=1.2)
+    elif name == "c4":
+        r = rng(4)
+        N = 4
+        a = np.ones((N, N))
+        iu = np.triu_indices(N, 1)
+        vals = r.uniform(0.5, 1.2, size=len(iu[0]))
+        a[iu] = vals
+        a[(iu[1], iu[0])] = vals
+        b = r.uniform(0.2, 0.35, size=N)
+        x = np.full(N, 0.25)
+        p = dict(lattice="D2Q9", nx=2048, ny=2048, ncomp=N, tau=1.0, a=a, b=b,
+                 kappa=np.full((N, N), 0.1), lam=_offdiag(N, 1.0),
+                 kT=0.8 * one_fluid_critical_kT(a, b, x), steps=5000, x=x, rho_total=1.3)
+    else:
+        raise KeyError(name)
+    p["gamma_mu"] = float(st.get("gamma_mu", 0.25))
+    p["width"] = float(st.get("width", 2.0))
+    p["name"] = name
+    return p
+
+
+def fields(name, nx=None, ny=None):
+    """Seeded initial densities rho [c][y][x] of workload ``name``.
+
+    ``nx``/``ny`` shrink the lattice (same recipe, same seed) for the sizes the
+    oracle finishes in seconds."""
+    p = base_params(name)
+    nx = int(nx or p["nx"])
+    ny = int(ny or p["ny"])
+    N = p["ncomp"]
+    if name == "c1":
+        # slab of total density 2.0 on the middle half, 0.2 elsewhere, x = 0.5,
+        # with tanh edges of the stored width, plus uniform noise in +-1e-3
+        r = rng(1)
+        xs = np.arange(nx, dtype=np.float64)
+        lo, hi = nx / 4.0 - 0.5, 3.0 * nx / 4.0 - 0.5
+        w = p["width"]
+        if w > 0:
+            tot = 0.2 + 1.8 * 0.5 * (np.tanh((xs - lo) / w) - np.tanh((xs - hi) / w))
+        else:
+            tot = np.where((xs > lo) & (xs < hi), 2.0, 0.2)
+        rho = np.stack([p["x"][c] * tot for c in range(N)])[:, None, :]
+        rho = rho + r.uniform(-1e-3, 1e-3, size=rho.shape)
+        return np.ascontiguousarray(rho)
+    if name in ("c2", "c5", "c4"):
+        r = rng({"c2": 2, "c5": 5, "c4": 4}[name])
+        if name == "c4":
+            r.uniform(0.5, 1.2, size=6)  # same stream position as base_params
+            r.uniform(0.2, 0.35, size=N)
+        mean = p["rho_total"] * p["x"]
+        rho = mean[:, None, None] + r.normal(0.0, 1e-2, size=(N, ny, nx))
+        return np.ascontiguousarray(rho)
+    raise KeyError(name)
+
+
+def uniform_noise_fields(ncomp, ny, nx, mean, sigma, seed_value):
+    """Uniform means plus Gaussian noise (used by small parity cases)."""
+    r = np.random.default_rng(seed_value)
+    mean = np.asarray(mean, dtype=np.float64).reshape(ncomp, 1, 1)
+    return np.ascontiguousarray(mean + r.normal(0.0, sigma, size=(ncomp, ny, nx)))
+
+
+def lib_kwargs(p, **over):
+    """Keyword arguments for ``paper_1805_07251_gb300.Simulation`` / ``oracle.Lattice``."""
+    kw = dict(lattice=p["lattice"], nx=p["nx"], ny=p["ny"], ncomp=p["ncomp"], tau=p["tau"],
+              kT=p["kT"], gamma_mu=p["gamma_mu"], a=p["a"], kappa=p["kappa"], lam=p["lam"], b=p["b"])
+    kw.update(over)
+    return kw

@@ -1,0 +1,99 @@
+"""Write lbinputs/params.json: gamma_mu and the initial slab width per workload.
+
+Calls only the CPU oracle (``oracle`` package) and the seeded input
+generators.  For each workload:
+  1. rho_l = total density of the densest coexisting phase at the mean
+     composition, from the oracle's convex-hull/Newton coexistence (two
+     components) or the mean total density (four components);
+  2. gamma_0 = (1 - c_s^2) / (4 kappa rho_l) with c_s^2 = 1/3 -- the interface
+     relation of Sec. V (Eq. kappaGammaMuRelation) solved for gamma_mu.  Under the
+     scaling (kT, a, kappa, gamma) ~ (theta, a theta/kT, kappa theta/kT, gamma kT/theta)
+     the kT factors cancel, so the same expression holds in kT units;
+  3. the first of gamma_0 x {1, 1/2, 1/4, ...} whose oracle run stays in the
+     domain (rho > 0, eta > 0) for the pre-scan horizon -- the practice of
+     Sec. VI of lowering gamma_mu by factors of 2-10 when a run is unstable.
+The slab width of workload c1 is sqrt(2 kappa / (theta_cr/kT - 1)) (Sec. V,
+interface width), raised to 2 lattice spacings (Sec. VI) when smaller.
+
+Run:  python tests/golden/make_config_params.py
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import lbinputs  # noqa: E402
+import oracle  # noqa: E402
+from oracle import thermo  # noqa: E402
+
+CS2 = 1.0 / 3.0
+
+
+def liquid_density(p):
+    if p["ncomp"] != 2:
+        return p.get("rho_total", 1.0)
+    mean = p.get("rho_total", 1.1) * p["x"] if p["name"] != "c1" else None
+    if p["name"] == "c1":
+        rho = lbinputs.fields("c1")
+        mean = rho.reshape(2, -1).mean(axis=1)
+    ph = thermo.coexistence(p["kT"], p["a"], p["b"], mean, n=500)
+    return max(float(np.sum(q)) for q in ph)
+
+
+def stable(p, gamma, nx, ny, steps):
+    L = oracle.Lattice(p["lattice"], nx, ny, p["ncomp"], p["tau"], p["kT"], gamma,
+                       p["a"], p["kappa"], p["lam"], p["b"])
+    f = L.equilibrium(lbinputs.fields(p["name"], nx=nx, ny=ny))
+    try:
+        L.run(f, steps)
+    except oracle.OracleDomainError:
+        return False
+    return True
+
+
+def main():
+    out = {}
+    plan = {"c1": (256, 1, 10000), "c2": (64, 64, 2000), "c5": (64, 64, 2000), "c4": (48, 48, 1000)}
+    for name, (nx, ny, steps) in plan.items():
+        p = lbinputs.base_params(name)
+        rec = {}
+        if name == "c1":
+            tcm = lbinputs.one_fluid_critical_kT(p["a"], p["b"], p["x"])
+            w = math.sqrt(2.0 * 0.1 / (tcm / p["kT"] - 1.0))
+            rec["width"] = max(2.0, w)
+            p["width"] = rec["width"]
+            # the width must be in place before fields() is called
+            out[name] = dict(rec)
+            with open(lbinputs.PARAMS_JSON, "w") as fh:
+                json.dump(out, fh, indent=1)
+        rl = liquid_density(p)
+        g0 = (1.0 - CS2) / (4.0 * float(p["kappa"][0, 0]) * rl)
+        rec["rho_l"] = rl
+        rec["gamma_0"] = g0
+        chosen = None
+        for k in range(8):
+            g = g0 / 2 ** k
+            ok = stable(p, g, nx, ny, steps)
+            print(name, "gamma", g, "stable" if ok else "left the domain", flush=True)
+            if ok:
+                chosen = g
+                break
+        if chosen is None:
+            raise SystemExit(f"{name}: no stable gamma_mu found")
+        rec["gamma_mu"] = chosen
+        rec["prescan"] = dict(nx=nx, ny=ny, steps=steps)
+        out[name] = rec
+        with open(lbinputs.PARAMS_JSON, "w") as fh:
+            json.dump(out, fh, indent=1)
+    print(json.dumps(out, indent=1))
+
+
+if __name__ == "__main__":
+    main()
