@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Benchmark of the fused multicomponent van der Waals lattice Boltzmann step.
+
+Workload (default): D2Q9, 2 components, 1024 x 1024 periodic, the asymmetric
+mixture a = [[1, .9], [.9, .6]], b = (.25, .3), kappa = .1, kT = 0.85 of the
+one-fluid critical temperature, uniform density 1.2 at mole fraction 0.4 plus
+seeded Gaussian noise (sigma 1e-2): spinodal decomposition.  One benchmark step
+is one lattice Boltzmann timestep (one fused kernel launch) of the whole
+lattice; the L2 is flushed (256 MB write) between timed steps, outside the
+timed events.
+
+Metric: component-MLUPS = ncomp * nodes * steps / s / 1e6, for the FP32-mixed
+path (headline ``value``) with the FP64 path measured in the same run
+(``fp64``), plus the roofline fraction of the step kernel against the measured
+HBM copy bandwidth.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With torchrun (N > 1) every rank runs an independent replica of the workload
+(the path has no exchange between independent runs); the timed region is
+bracketed by barriers and the maximum over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "component-MLUPS"
+UNIT = "component-MLUPS"
+WORKLOAD = "c2"
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        with open(self.tmp.name) as fh:
+            rows = [r.strip().split(",") for r in fh if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline_oracle(kw, rho_full, nx, steps):
+    """Time the CPU oracle (as it stands) on an nx x nx sample of the same recipe."""
+    import numpy as np
+
+    import lbinputs
+    import oracle
+
+    rho = lbinputs.fields(WORKLOAD, nx=nx, ny=nx)
+    L = oracle.Lattice(kw["lattice"], nx, nx, kw["ncomp"], kw["tau"], kw["kT"], kw["gamma_mu"], kw["a"],
+                       kw["kappa"], kw["lam"], kw["b"])
+    f = L.equilibrium(rho)
+    t0 = time.perf_counter()
+    L.run(f, steps)
+    dt = time.perf_counter() - t0
+    value = kw["ncomp"] * nx * nx * steps / dt / 1e6
+    del np
+    return value, dt
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on the same workload, one oracle timestep of the
+    full 1024 x 1024 lattice per benchmark step."""
+    import lbinputs
+    import oracle
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    p = lbinputs.base_params(WORKLOAD)
+    kw = lbinputs.lib_kwargs(p)
+    rho = lbinputs.fields(WORKLOAD)
+    L = oracle.Lattice(kw["lattice"], kw["nx"], kw["ny"], kw["ncomp"], kw["tau"], kw["kT"], kw["gamma_mu"], kw["a"],
+                       kw["kappa"], kw["lam"], kw["b"])
+    f = L.equilibrium(rho)
+    f = L.run(f, args.warmup)
+    t0 = time.perf_counter()
+    L.run(f, args.steps)
+    dt = time.perf_counter() - t0
+    nodes = kw["nx"] * kw["ny"]
+    value = kw["ncomp"] * nodes * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "D2Q9, 2 components, 1024x1024 periodic, spinodal mixture (c2)",
+                   "nodes": nodes, "ncomp": kw["ncomp"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"full 1024x1024 lattice, {args.steps} oracle timesteps after {args.warmup} warm-up"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_path(torch, Simulation, kw, rho, precision, steps, warmup, flush, dev):
+    """Device time of the fused step kernel: CUDA events on the launching stream around
+    each step, L2 flushed before each step outside the events."""
+    stream = torch.cuda.current_stream(dev)
+    sim = Simulation(precision=precision, device=dev, stream=stream.cuda_stream, **kw)
+    sim.init(rho)
+    for _ in range(warmup):
+        flush.zero_()
+        sim.step(1)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    launches0 = sim.launches
+    return sim, ev, launches0, stream
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.warmup < 3:
+        args.warmup = 3
+
+    import numpy as np
+    import torch
+
+    import lbinputs
+    from paper_1805_07251_gb300 import Simulation, build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = local
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    build.build()
+
+    p = lbinputs.base_params(WORKLOAD)
+    kw = lbinputs.lib_kwargs(p)
+    rho = lbinputs.fields(WORKLOAD)
+    N, nodes = kw["ncomp"], kw["nx"] * kw["ny"]
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    peak_gbs, peak_kind = read_peaks()
+
+    results = {}
+    clocks = None
+    for precision in (["fp32_mixed"] if args.no_fp64 else ["fp32_mixed", "fp64"]):
+        sim, ev, l0, stream = time_path(torch, Simulation, kw, rho, precision, args.steps, args.warmup, flush, dev)
+        sampler = ClockSampler(dev) if precision == "fp32_mixed" else None
+        if sampler:
+            sampler.start()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            sim.step(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        if sampler:
+            clocks = sampler.stop()
+        launches = sim.launches - l0
+        per = [a.elapsed_time(b) for a, b in ev]
+        total_ms = float(sum(per))
+        if dist is not None:
+            t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        ms = total_ms / args.steps
+        value = world * N * nodes * args.steps / (total_ms * 1e-3) / 1e6
+        elem = 4 if precision == "fp32_mixed" else 8
+        alg_bytes = N * nodes * 9 * 2 * elem
+        achieved = alg_bytes / (ms * 1e-3) / 1e9
+        results[precision] = dict(value=value, ms=ms, launches=launches, alg_bytes=alg_bytes, achieved=achieved)
+        sim.close()
+
+    # end to end through the C ABI with host buffers: pinned host densities in,
+    # K timesteps, densities and momenta back to pinned host memory
+    sim = Simulation(precision="fp32_mixed", device=dev, stream=torch.cuda.current_stream(dev).cuda_stream, **kw)
+    h_rho = torch.from_numpy(rho).pin_memory().numpy()
+    o_rho = torch.empty(rho.shape, dtype=torch.float64).pin_memory().numpy()
+    o_mom = torch.empty((N, 2) + rho.shape[1:], dtype=torch.float64).pin_memory().numpy()
+    from paper_1805_07251_gb300 import capi
+
+    sim.init(h_rho)
+    sim.step(args.warmup)
+    capi.lb_read_moments(sim.ctx, o_rho, o_mom)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    capi.lb_init_fields(sim.ctx, h_rho)
+    sim.step(args.steps)
+    capi.lb_read_moments(sim.ctx, o_rho, o_mom)
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    sim.close()
+    e2e = {"value": world * N * nodes * args.steps / e2e_s / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": int(rho.nbytes // args.steps),
+           "d2h_bytes_per_step": int((o_rho.nbytes + o_mom.nbytes) // args.steps),
+           "note": "per-step bytes amortise one host->device field upload and one device->host "
+                   "read of densities and momenta over the K timesteps of the job"}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    head = results["fp32_mixed"]
+    line = {
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 populations, f64 mu", "data": "synthetic",
+        "config": {"workload": "D2Q9, 2 components, 1024x1024 periodic, spinodal mixture (c2), FP32-mixed",
+                   "nodes": nodes, "ncomp": N, "tile": "32x8", "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "independent replica per GPU" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": head["achieved"], "peak": peak_gbs, "unit": "GB/s",
+                     "frac": head["achieved"] / peak_gbs, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "lb_step_kernel<D2Q9, N=2, 32x8, float>",
+                     "alg_bytes_per_launch": head["alg_bytes"]},
+        "gpu_launches": head["launches"],
+        "e2e": e2e,
+    }
+    if "fp64" in results:
+        r64 = results["fp64"]
+        line["fp64"] = {"value": r64["value"], "unit": UNIT, "ms_per_step": r64["ms"],
+                        "roofline_hbm": {"achieved": r64["achieved"], "peak": peak_gbs, "unit": "GB/s",
+                                         "frac": r64["achieved"] / peak_gbs}}
+        line["gpu_launches"] += r64["launches"]
+    if clocks:
+        line["clocks"] = clocks
+    if world == 1 and not args.no_cpu_baseline:
+        ncb = 256
+        steps_cb = 100
+        v, dt = cpu_baseline_oracle(kw, rho, ncb, steps_cb)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{ncb}x{ncb} lattice of the same recipe, {steps_cb} oracle timesteps "
+                                          f"({dt:.1f} s, single thread)"}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    del np
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,177 @@
+/*
+ * lbvdw.h -- C ABI of the GB300 lattice Boltzmann library for N-component
+ * van der Waals mixtures (Ridl & Wagner, "Lattice Boltzmann simulation of
+ * mixtures with multicomponent van der Waals equation of state",
+ * arXiv:1805.07251).
+ *
+ * One timestep (lb_step) performs, per node and component c, in one fused
+ * CUDA kernel:
+ *   1. moments rho^c = sum_i f_i^c and rho^c u^c = sum_i f_i^c v_i        (Sec. III)
+ *   2. chemical potential
+ *        mu^c = kT [ln(rho^c/eta) + b^c rho/eta] - sum_c' [2 a^{cc'} rho^c' + kappa^{cc'} Lap rho^c'],
+ *      eta = 1 - sum_c b^c rho^c, rho = sum_c rho^c  (Eq. discreteChemicalPotential with
+ *      the interaction function psi of Eqs. a-psi, kappa-psi and Sec. V folded into a
+ *      lattice Laplacian)
+ *   3. mean-field force gained by component c:
+ *        "log" (Eq. forceMuLog):  G^{mu,c} = -gamma_mu rho^c D mu^c + theta D rho^c
+ *        "nid" (Eq. forceMuId):   G^{mu,c} = -rho^c D (gamma_mu mu^c - theta ln rho^c)
+ *   4. friction between components with the implicit velocity u-hat (Eq. forceFriction),
+ *      solved exactly per node
+ *   5. Psi correction (Eq. forceCorrectionsPsi)
+ *   6. BGK collision towards the Hermite equilibrium (Eqs. BGKcollisionOperator, feq)
+ *      plus the forcing populations with moments 0, G and G u + u G - Psi (Sec. III and
+ *      the explicit D1Q3 update of Sec. V)
+ *   7. streaming (Eq. LBequation), periodic in every direction.
+ * theta = 1/3 is the lattice temperature (sound speed squared); kT is the
+ * thermodynamic temperature in mu, p and F.  D is the central difference
+ * (1/theta) sum_i w_i v_i phi(x + v_i), Lap the lattice Laplacian
+ * (2/theta) sum_i w_i (phi(x + v_i) - phi(x)); in D1Q3 these are the central
+ * difference and the three-point Laplacian of Sec. V.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an lb_status; no C++ exception crosses this boundary.
+ *   - Host arrays belong to the caller; the library copies in and out.  Device
+ *     buffers of a context belong to the context until lb_destroy.
+ *   - Field layouts (x fastest):  rho [c][y][x];  mom [c][d][y][x] with d = 0 (x),
+ *     1 (y, D2Q9 only);  populations [c][i][y][x].
+ *   - Lattice velocity order:  D1Q3: 0, +1, -1.  D2Q9: (0,0) (1,0) (0,1) (-1,0) (0,-1)
+ *     (1,1) (-1,1) (-1,-1) (1,-1), weights 4/9, 1/9 x4, 1/36 x4.
+ *   - Calls that read results back (lb_read_moments, lb_free_energy, lb_save_state)
+ *     synchronise the context's stream and report any error the step kernels flagged
+ *     since the last such call.  lb_step is asynchronous.
+ *   - After LB_E_DOMAIN, LB_E_CUDA or LB_E_TIMEOUT the context is poisoned: every call
+ *     but lb_init_fields*, lb_load_state, lb_last_error and lb_destroy returns LB_E_STATE
+ *     until the fields are set again.
+ *   - One context must not be used from two host threads at the same time.
+ */
+#ifndef LBVDW_H
+#define LBVDW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBVDW_ABI 1
+
+typedef enum {
+    LB_OK = 0,
+    LB_E_INVALID = 1, /* bad argument or parameter set */
+    LB_E_NOMEM = 2,   /* device or host allocation failed */
+    LB_E_CUDA = 3,    /* a CUDA call failed; lb_last_error names it */
+    LB_E_DOMAIN = 4,  /* rho^c <= 0, eta <= 0 or a non-finite value met in a step */
+    LB_E_TIMEOUT = 5, /* a bounded device-side wait ran out */
+    LB_E_STATE = 6    /* call out of order, or context poisoned */
+} lb_status;
+
+typedef enum { LB_D1Q3 = 1, LB_D2Q9 = 2 } lb_lattice;
+
+typedef enum {
+    LB_FP64 = 0,      /* populations and all arithmetic in FP64 */
+    LB_FP32_MIXED = 1 /* FP32 populations stored as deviations f_i - w_i rho_ref^c,
+                         FP64 in mu^c (eta, 1/eta, logs) and in mass sums */
+} lb_precision;
+
+typedef enum { LB_FORCE_LOG = 0, LB_FORCE_NID = 1 } lb_force_method;
+
+typedef struct {
+    uint32_t abi;        /* must equal LBVDW_ABI */
+    int32_t lattice;     /* lb_lattice */
+    int32_t nx, ny;      /* nodes; ny == 1 for D1Q3; nx, ny >= 2 otherwise (nx >= 2 for D1Q3) */
+    int32_t ncomp;       /* 1..4 components */
+    int32_t precision;   /* lb_precision */
+    int32_t force_method;/* lb_force_method */
+    int32_t check_every; /* >0: lb_step synchronises and checks the error word every
+                            check_every steps; 0: only calls that read back check it */
+    double tau;          /* BGK relaxation time, > 1/2 */
+    double kT;           /* thermodynamic temperature in mu, p, F; > 0 */
+    double gamma_mu;     /* prefactor of mu in the force (Eq. forceMuNid); > 0 */
+    double a[16];        /* a^{cc'} (Eq. a-psi), row major with row stride 4, symmetric */
+    double kappa[16];    /* kappa^{cc'} (Eq. kappa-psi), stride 4, symmetric */
+    double lambda[16];   /* friction lambda^{cc'} (Eq. forceFriction), stride 4, symmetric,
+                            >= 0; diagonal ignored */
+    double b[4];         /* excluded volume b^c > 0 */
+    double rho_ref[4];   /* LB_FP32_MIXED only: reference density of component c whose
+                            rest equilibrium is subtracted before FP32 storage; 0 = use
+                            the mean density set by lb_init_fields */
+    int32_t device;      /* CUDA device ordinal */
+    int32_t tile_x, tile_y; /* 0 = library default / autotuned choice */
+    void *stream;        /* cudaStream_t for every launch and copy; NULL = legacy default */
+} lb_params;
+
+typedef struct lb_ctx lb_ctx;
+
+/* Fill *p with defaults: abi, D2Q9, 64 x 64, 2 components, FP64, "log", tau = 1,
+ * kT = 1/3, gamma_mu = 1, a = 0, kappa = 0, lambda = 0, b = 0 (so callers must set
+ * b before lb_create). */
+void lb_default_params(lb_params *p);
+
+/* Validate *p (symmetry of a, kappa, lambda; b > 0; tau > 1/2; sizes) and create a
+ * context on p->device: allocates two population buffers, a moments buffer and a
+ * diagnostics scratch area with cudaMalloc.  No kernel runs.  On success *out owns
+ * those buffers.  Errors: LB_E_INVALID, LB_E_NOMEM, LB_E_CUDA. */
+lb_status lb_create(const lb_params *p, lb_ctx **out);
+
+/* Set the state to the equilibrium (Eq. feq, at theta = 1/3) of host densities
+ * rho [c][y][x] and momenta mom [c][d][y][x] (bare rho^c u^c; NULL = at rest).
+ * Synchronous.  Clears the error word and the poisoned flag.
+ * Errors: LB_E_INVALID (NULL ctx/rho), LB_E_DOMAIN (a density <= 0 or eta <= 0:
+ * the state is left unset), LB_E_CUDA. */
+lb_status lb_init_fields(lb_ctx *ctx, const double *rho, const double *mom);
+
+/* Same as lb_init_fields with device pointers (FP64, same layouts), enqueued on the
+ * context stream; the caller keeps the buffers alive until the stream reaches it.
+ * The domain check of the densities is deferred to the next read-back call. */
+lb_status lb_init_fields_dev(lb_ctx *ctx, const double *rho_dev, const double *mom_dev);
+
+/* Enqueue nsteps >= 0 timesteps on the context stream.  Asynchronous unless
+ * check_every > 0.  Errors: LB_E_STATE, LB_E_INVALID, LB_E_CUDA, LB_E_DOMAIN (only
+ * when check_every > 0). */
+lb_status lb_step(lb_ctx *ctx, int64_t nsteps);
+
+/* Copy rho^c [c][y][x] and bare momenta j^c = sum_i f_i^c v_i [c][d][y][x] of the
+ * current state to host arrays (mom may be NULL).  The physical velocity of Sec. III
+ * is u-hat^c = j^c/rho^c + G^c/(2 rho^c).  Synchronises; reports flagged errors. */
+lb_status lb_read_moments(lb_ctx *ctx, double *rho, double *mom);
+
+/* Device-pointer variant of lb_read_moments (FP64 outputs), enqueued on the context
+ * stream; does not synchronise or check the error word. */
+lb_status lb_read_moments_dev(lb_ctx *ctx, double *rho_dev, double *mom_dev);
+
+/* Lattice free energy of Eq. discreteFreeEnergy of the current densities,
+ *   F = sum_x [ sum_c kT rho^c ln(rho^c/eta) - sum_cc' a^{cc'} rho^c rho^c'
+ *               - 1/2 sum_cc' kappa^{cc'} rho^c Lap rho^c' ],
+ * per-component mass sum_x rho^c (mass[ncomp], may be NULL) and total momentum
+ * sum_x sum_c j^c (mom_total[2], may be NULL), all reduced in FP64 in a fixed order
+ * (one partial per CTA, then one CTA), so results are bitwise reproducible.
+ * Synchronises; reports flagged errors. */
+lb_status lb_free_energy(lb_ctx *ctx, double *F, double *mass, double *mom_total);
+
+/* Size in bytes of a saved state, and save/load of the raw populations
+ * ([c][i][y][x] in the storage type of the precision, plus a 64-byte header with the
+ * step counter and a parameter hash).  lb_save_state synchronises; lb_load_state
+ * checks the header against the context (LB_E_INVALID on mismatch). */
+size_t lb_state_bytes(const lb_ctx *ctx);
+lb_status lb_save_state(lb_ctx *ctx, void *host_buf, size_t bytes);
+lb_status lb_load_state(lb_ctx *ctx, const void *host_buf, size_t bytes);
+
+/* Number of timesteps taken since the state was last set (lb_init_fields,
+ * lb_init_fields_dev or lb_load_state). */
+int64_t lb_step_count(const lb_ctx *ctx);
+
+/* Kernel launches enqueued by this context since creation (for launch accounting). */
+int64_t lb_launch_count(const lb_ctx *ctx);
+
+/* Release every device buffer of the context and the context itself (NULL is a no-op). */
+lb_status lb_destroy(lb_ctx *ctx);
+
+/* Static text of a status; last error message of a context (never NULL). */
+const char *lb_status_str(lb_status s);
+const char *lb_last_error(const lb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBVDW_H */

@@ -1,0 +1,190 @@
+"""ctypes binding of the C ABI in include/lbvdw.h (argument marshalling only).
+
+Every function keeps the C name and signature; arrays are passed as NumPy
+host arrays (``lb_init_fields``, ``lb_read_moments`` ...) or as raw device
+addresses (``*_dev``), e.g. ``torch.Tensor.data_ptr()``.  The library is the
+in-tree ``_lib/liblbvdw.so`` built by ``build.py``; loading fails loudly if it
+is missing -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "liblbvdw.so")
+
+LBVDW_ABI = 1
+LB_OK, LB_E_INVALID, LB_E_NOMEM, LB_E_CUDA, LB_E_DOMAIN, LB_E_TIMEOUT, LB_E_STATE = range(7)
+LB_D1Q3, LB_D2Q9 = 1, 2
+LB_FP64, LB_FP32_MIXED = 0, 1
+LB_FORCE_LOG, LB_FORCE_NID = 0, 1
+
+
+class lb_params(ctypes.Structure):
+    _fields_ = [
+        ("abi", ctypes.c_uint32),
+        ("lattice", ctypes.c_int32),
+        ("nx", ctypes.c_int32),
+        ("ny", ctypes.c_int32),
+        ("ncomp", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("force_method", ctypes.c_int32),
+        ("check_every", ctypes.c_int32),
+        ("tau", ctypes.c_double),
+        ("kT", ctypes.c_double),
+        ("gamma_mu", ctypes.c_double),
+        ("a", ctypes.c_double * 16),
+        ("kappa", ctypes.c_double * 16),
+        ("lambda_", ctypes.c_double * 16),
+        ("b", ctypes.c_double * 4),
+        ("rho_ref", ctypes.c_double * 4),
+        ("device", ctypes.c_int32),
+        ("tile_x", ctypes.c_int32),
+        ("tile_y", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+class LBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_str(status)}: {msg}")
+        self.status = status
+
+
+def load():
+    """Load liblbvdw.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                           "(run paper_1805_07251_gb300.build.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER(lb_params)
+    C = ctypes.c_void_p
+    sig = {
+        "lb_default_params": (None, [P]),
+        "lb_create": (ctypes.c_int, [P, ctypes.POINTER(C)]),
+        "lb_init_fields": (ctypes.c_int, [C, _DP, _DP]),
+        "lb_init_fields_dev": (ctypes.c_int, [C, C, C]),
+        "lb_step": (ctypes.c_int, [C, ctypes.c_int64]),
+        "lb_read_moments": (ctypes.c_int, [C, _DP, _DP]),
+        "lb_read_moments_dev": (ctypes.c_int, [C, C, C]),
+        "lb_free_energy": (ctypes.c_int, [C, _DP, _DP, _DP]),
+        "lb_state_bytes": (ctypes.c_size_t, [C]),
+        "lb_save_state": (ctypes.c_int, [C, C, ctypes.c_size_t]),
+        "lb_load_state": (ctypes.c_int, [C, C, ctypes.c_size_t]),
+        "lb_step_count": (ctypes.c_int64, [C]),
+        "lb_launch_count": (ctypes.c_int64, [C]),
+        "lb_destroy": (ctypes.c_int, [C]),
+        "lb_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+        "lb_last_error": (ctypes.c_char_p, [C]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_str(s):
+    return load().lb_status_str(int(s)).decode()
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(_DP)
+
+
+def _check(ctx, rc, what):
+    if rc != LB_OK:
+        msg = load().lb_last_error(ctx).decode() if ctx else ""
+        raise LBError(rc, f"{what}: {msg}")
+
+
+# --- thin wrappers with the C names -----------------------------------------
+
+def lb_default_params():
+    p = lb_params()
+    load().lb_default_params(ctypes.byref(p))
+    return p
+
+
+def lb_create(p):
+    out = ctypes.c_void_p()
+    rc = load().lb_create(ctypes.byref(p), ctypes.byref(out))
+    if rc != LB_OK:
+        raise LBError(rc, "lb_create rejected the parameters")
+    return out
+
+
+def lb_init_fields(ctx, rho, mom=None):
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    mom = None if mom is None else np.ascontiguousarray(mom, dtype=np.float64)
+    _check(ctx, load().lb_init_fields(ctx, _dp(rho), _dp(mom)), "lb_init_fields")
+
+
+def lb_init_fields_dev(ctx, rho_ptr, mom_ptr=None):
+    _check(ctx, load().lb_init_fields_dev(ctx, ctypes.c_void_p(rho_ptr),
+                                          ctypes.c_void_p(mom_ptr) if mom_ptr else None),
+           "lb_init_fields_dev")
+
+
+def lb_step(ctx, nsteps):
+    _check(ctx, load().lb_step(ctx, int(nsteps)), "lb_step")
+
+
+def lb_read_moments(ctx, rho_out, mom_out=None):
+    _check(ctx, load().lb_read_moments(ctx, _dp(rho_out), _dp(mom_out)), "lb_read_moments")
+
+
+def lb_read_moments_dev(ctx, rho_ptr, mom_ptr=None):
+    _check(ctx, load().lb_read_moments_dev(ctx, ctypes.c_void_p(rho_ptr),
+                                           ctypes.c_void_p(mom_ptr) if mom_ptr else None),
+           "lb_read_moments_dev")
+
+
+def lb_free_energy(ctx, ncomp):
+    F = np.zeros(1)
+    mass = np.zeros(ncomp)
+    mom = np.zeros(2)
+    _check(ctx, load().lb_free_energy(ctx, _dp(F), _dp(mass), _dp(mom)), "lb_free_energy")
+    return float(F[0]), mass, mom
+
+
+def lb_state_bytes(ctx):
+    return int(load().lb_state_bytes(ctx))
+
+
+def lb_save_state(ctx):
+    buf = np.empty(lb_state_bytes(ctx), dtype=np.uint8)
+    _check(ctx, load().lb_save_state(ctx, buf.ctypes.data, buf.nbytes), "lb_save_state")
+    return buf
+
+
+def lb_load_state(ctx, buf):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(ctx, load().lb_load_state(ctx, buf.ctypes.data, buf.nbytes), "lb_load_state")
+
+
+def lb_step_count(ctx):
+    return int(load().lb_step_count(ctx))
+
+
+def lb_launch_count(ctx):
+    return int(load().lb_launch_count(ctx))
+
+
+def lb_destroy(ctx):
+    load().lb_destroy(ctx)
+
+
+def lb_last_error(ctx):
+    return load().lb_last_error(ctx).decode()

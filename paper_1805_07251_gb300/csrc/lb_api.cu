@@ -1,0 +1,484 @@
+// lb_api.cu -- the C ABI declared in include/lbvdw.h: context management,
+// argument validation, launches on the context stream and read-back.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "lbvdw.h"
+#include "lb_launch.cuh"
+
+using namespace lbvdw;
+
+struct lb_ctx {
+    lb_params p;
+    int Q = 0, D = 0;
+    size_t n = 0;      // nodes
+    size_t elem = 0;   // bytes per stored population
+    void *f[2] = {nullptr, nullptr};
+    int cur = 0;
+    double *rho = nullptr;  // moments scratch [N][n]
+    double *mom = nullptr;  // moments scratch [N][D][n]
+    double *partial = nullptr;
+    int nparts = 0;
+    double *diag = nullptr;  // [N + 3]
+    unsigned *err = nullptr;
+    cudaStream_t stream = nullptr;
+    DevParams dp{};
+    int64_t steps = 0, launches = 0;
+    bool has_state = false, poisoned = false;
+    std::string msg;
+};
+
+namespace {
+
+const char *k_status[] = {"LB_OK", "LB_E_INVALID", "LB_E_NOMEM", "LB_E_CUDA",
+                          "LB_E_DOMAIN", "LB_E_TIMEOUT", "LB_E_STATE"};
+
+lb_status fail(lb_ctx *c, lb_status s, const std::string &m) {
+    if (c) {
+        c->msg = m;
+        if (s == LB_E_DOMAIN || s == LB_E_CUDA || s == LB_E_TIMEOUT) c->poisoned = true;
+    }
+    return s;
+}
+
+lb_status cuda_fail(lb_ctx *c, cudaError_t e, const char *where) {
+    return fail(c, LB_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LB_CUDA(ctx, call)                                         \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+bool symmetric(const double *m, int N) {
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j)
+            if (m[i * 4 + j] != m[j * 4 + i]) return false;
+    return true;
+}
+
+bool finite_all(const double *m, int cnt) {
+    for (int i = 0; i < cnt; ++i)
+        if (!std::isfinite(m[i])) return false;
+    return true;
+}
+
+cudaError_t run_step(lb_ctx *c) {
+    StepLaunch a;
+    a.fin = c->f[c->cur];
+    a.fout = c->f[c->cur ^ 1];
+    a.P = c->dp;
+    a.ncomp = c->p.ncomp;
+    a.force = c->p.force_method;
+    a.tile_x = c->p.tile_x;
+    a.tile_y = c->p.tile_y;
+    a.stream = c->stream;
+    bool mixed = c->p.precision == LB_FP32_MIXED;
+    if (c->p.lattice == LB_D1Q3) return mixed ? d1q3_mixed_step(a) : d1q3_f64_step(a);
+    return mixed ? d2q9_mixed_step(a) : d2q9_f64_step(a);
+}
+
+FieldLaunch field_args(lb_ctx *c) {
+    FieldLaunch a;
+    a.f = c->f[c->cur];
+    a.rho_in = c->rho;
+    a.mom_in = nullptr;
+    a.rho_out = c->rho;
+    a.mom_out = c->mom;
+    a.partial = c->partial;
+    a.nparts = c->nparts;
+    a.diag_out = c->diag;
+    a.P = c->dp;
+    a.ncomp = c->p.ncomp;
+    a.stream = c->stream;
+    return a;
+}
+
+cudaError_t run_field(lb_ctx *c, int which, const FieldLaunch &a) {
+    bool mixed = c->p.precision == LB_FP32_MIXED;
+    bool d1 = c->p.lattice == LB_D1Q3;
+    switch (which) {
+        case 0: return d1 ? (mixed ? d1q3_mixed_init(a) : d1q3_f64_init(a)) : (mixed ? d2q9_mixed_init(a) : d2q9_f64_init(a));
+        case 1: return d1 ? (mixed ? d1q3_mixed_moments(a) : d1q3_f64_moments(a)) : (mixed ? d2q9_mixed_moments(a) : d2q9_f64_moments(a));
+        default: return d1 ? (mixed ? d1q3_mixed_diag(a) : d1q3_f64_diag(a)) : (mixed ? d2q9_mixed_diag(a) : d2q9_f64_diag(a));
+    }
+}
+
+// Synchronise the stream and turn a flagged device error into a status.
+lb_status sync_check(lb_ctx *c) {
+    unsigned h = 0;
+    LB_CUDA(c, cudaMemcpyAsync(&h, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (h & ERR_DOMAIN) return fail(c, LB_E_DOMAIN, "a density or eta <= 0, or a non-finite value, was met");
+    return LB_OK;
+}
+
+lb_status usable(lb_ctx *c) {
+    if (!c) return LB_E_INVALID;
+    if (c->poisoned) return fail(c, LB_E_STATE, "context poisoned by an earlier error; set the fields again");
+    if (!c->has_state) return fail(c, LB_E_STATE, "fields not initialised");
+    cudaError_t e = cudaSetDevice(c->p.device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return LB_OK;
+}
+
+uint64_t params_hash(const lb_params &p) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&h](const void *d, size_t nb) {
+        const unsigned char *b = static_cast<const unsigned char *>(d);
+        for (size_t i = 0; i < nb; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+    };
+    mix(&p.lattice, sizeof p.lattice); mix(&p.nx, sizeof p.nx); mix(&p.ny, sizeof p.ny);
+    mix(&p.ncomp, sizeof p.ncomp); mix(&p.precision, sizeof p.precision);
+    mix(&p.tau, sizeof p.tau); mix(&p.kT, sizeof p.kT); mix(&p.gamma_mu, sizeof p.gamma_mu);
+    mix(p.a, sizeof p.a); mix(p.kappa, sizeof p.kappa); mix(p.lambda, sizeof p.lambda); mix(p.b, sizeof p.b);
+    return h;
+}
+
+struct StateHeader {
+    char magic[8];
+    uint32_t abi, lattice;
+    int32_t nx, ny, ncomp, precision;
+    int64_t steps;
+    uint64_t hash;
+    double rho_ref_sum;
+    char pad[8];
+};
+static_assert(sizeof(StateHeader) == 64, "state header is 64 bytes");
+
+}  // namespace
+
+extern "C" {
+
+void lb_default_params(lb_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->abi = LBVDW_ABI;
+    p->lattice = LB_D2Q9;
+    p->nx = 64;
+    p->ny = 64;
+    p->ncomp = 2;
+    p->precision = LB_FP64;
+    p->force_method = LB_FORCE_LOG;
+    p->tau = 1.0;
+    p->kT = 1.0 / 3.0;
+    p->gamma_mu = 1.0;
+}
+
+lb_status lb_create(const lb_params *p, lb_ctx **out) {
+    if (!p || !out) return LB_E_INVALID;
+    *out = nullptr;
+    const int N = p->ncomp;
+    if (p->abi != LBVDW_ABI) return LB_E_INVALID;
+    if (p->lattice != LB_D1Q3 && p->lattice != LB_D2Q9) return LB_E_INVALID;
+    if (N < 1 || N > 4) return LB_E_INVALID;
+    if (p->precision != LB_FP64 && p->precision != LB_FP32_MIXED) return LB_E_INVALID;
+    if (p->force_method != LB_FORCE_LOG && p->force_method != LB_FORCE_NID) return LB_E_INVALID;
+    if (p->nx < 2) return LB_E_INVALID;
+    if (p->lattice == LB_D1Q3 ? p->ny != 1 : p->ny < 2) return LB_E_INVALID;
+    if ((int64_t)p->nx * p->ny > (int64_t)1 << 31) return LB_E_INVALID;
+    if (!(p->tau > 0.5) || !(p->kT > 0.0) || !(p->gamma_mu > 0.0) || !std::isfinite(p->tau) ||
+        !std::isfinite(p->kT) || !std::isfinite(p->gamma_mu))
+        return LB_E_INVALID;
+    if (!finite_all(p->a, 16) || !finite_all(p->kappa, 16) || !finite_all(p->lambda, 16) || !finite_all(p->b, 4) ||
+        !finite_all(p->rho_ref, 4))
+        return LB_E_INVALID;
+    if (!symmetric(p->a, N) || !symmetric(p->kappa, N) || !symmetric(p->lambda, N)) return LB_E_INVALID;
+    for (int c = 0; c < N; ++c) {
+        if (!(p->b[c] > 0.0) || p->rho_ref[c] < 0.0) return LB_E_INVALID;
+        for (int cc = 0; cc < N; ++cc)
+            if (cc != c && p->lambda[c * 4 + cc] < 0.0) return LB_E_INVALID;
+    }
+    if (p->check_every < 0) return LB_E_INVALID;
+
+    lb_ctx *c = new (std::nothrow) lb_ctx;
+    if (!c) return LB_E_NOMEM;
+    c->p = *p;
+    if (c->p.tile_x == 0 && c->p.tile_y == 0) {
+        c->p.tile_x = p->lattice == LB_D1Q3 ? 128 : 32;
+        c->p.tile_y = p->lattice == LB_D1Q3 ? 1 : 8;
+    }
+    bool tile_ok = p->lattice == LB_D1Q3
+                       ? (c->p.tile_y == 1 && (c->p.tile_x == 128 || c->p.tile_x == 256))
+                       : ((c->p.tile_x == 32 && c->p.tile_y == 8) || (c->p.tile_x == 64 && c->p.tile_y == 4) ||
+                          (c->p.tile_x == 32 && c->p.tile_y == 16));
+    if (!tile_ok) { delete c; return LB_E_INVALID; }
+    c->Q = p->lattice == LB_D1Q3 ? 3 : 9;
+    c->D = p->lattice == LB_D1Q3 ? 1 : 2;
+    c->n = (size_t)p->nx * p->ny;
+    c->elem = p->precision == LB_FP64 ? sizeof(double) : sizeof(float);
+    c->stream = static_cast<cudaStream_t>(p->stream);
+
+    cudaError_t e = cudaSetDevice(p->device);
+    if (e != cudaSuccess) { delete c; return LB_E_CUDA; }
+    size_t fbytes = c->elem * (size_t)N * c->Q * c->n;
+    size_t nparts = (c->n + DIAG_THREADS - 1) / DIAG_THREADS;
+    if (nparts > 152 * 8) nparts = 152 * 8;
+    c->nparts = (int)nparts;
+    bool ok = cudaMalloc(&c->f[0], fbytes) == cudaSuccess && cudaMalloc(&c->f[1], fbytes) == cudaSuccess &&
+              cudaMalloc(&c->rho, sizeof(double) * N * c->n) == cudaSuccess &&
+              cudaMalloc(&c->mom, sizeof(double) * N * c->D * c->n) == cudaSuccess &&
+              cudaMalloc(&c->partial, sizeof(double) * (N + 3) * nparts) == cudaSuccess &&
+              cudaMalloc(&c->diag, sizeof(double) * (N + 3)) == cudaSuccess &&
+              cudaMalloc(&c->err, sizeof(unsigned)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        lb_destroy(c);
+        return LB_E_NOMEM;
+    }
+    DevParams &d = c->dp;
+    d.nx = p->nx;
+    d.ny = p->ny;
+    d.omega = 1.0 / p->tau;
+    d.psi_g = (p->tau - 0.25) / p->tau;
+    d.psi_l = 1.0 / (12.0 * p->tau);
+    d.kT = p->kT;
+    d.gamma = p->gamma_mu;
+    for (int k = 0; k < 16; ++k) {
+        d.a[k] = p->a[k];
+        d.kappa[k] = p->kappa[k];
+        d.lam[k] = p->lambda[k];
+    }
+    for (int k = 0; k < 4; ++k) {
+        d.b[k] = p->b[k];
+        d.rho_ref[k] = 0.0;
+    }
+    d.err = c->err;
+    *out = c;
+    return LB_OK;
+}
+
+static lb_status init_common(lb_ctx *c, const double *rho_dev, const double *mom_dev, const double *rho_ref) {
+    const int N = c->p.ncomp;
+    for (int k = 0; k < 4; ++k) c->dp.rho_ref[k] = 0.0;
+    if (c->p.precision == LB_FP32_MIXED)
+        for (int k = 0; k < N; ++k) c->dp.rho_ref[k] = c->p.rho_ref[k] > 0.0 ? c->p.rho_ref[k] : rho_ref[k];
+    LB_CUDA(c, cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+    c->cur = 0;
+    FieldLaunch a = field_args(c);
+    a.rho_in = rho_dev;
+    a.mom_in = mom_dev;
+    a.P = c->dp;
+    cudaError_t e = run_field(c, 0, a);
+    if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+    c->launches += 1;
+    c->steps = 0;
+    c->has_state = true;
+    c->poisoned = false;
+    c->msg.clear();
+    return LB_OK;
+}
+
+lb_status lb_init_fields(lb_ctx *c, const double *rho, const double *mom) {
+    if (!c || !rho) return LB_E_INVALID;
+    const int N = c->p.ncomp;
+    LB_CUDA(c, cudaSetDevice(c->p.device));
+    double mean[4] = {0, 0, 0, 0};
+    for (size_t s = 0; s < c->n; ++s) {
+        double eta = 1.0;
+        for (int k = 0; k < N; ++k) {
+            double r = rho[k * c->n + s];
+            if (!(r > 0.0) || !std::isfinite(r)) {
+                c->has_state = false;
+                return fail(c, LB_E_DOMAIN, "a density is <= 0 or not finite");
+            }
+            eta -= c->p.b[k] * r;
+            mean[k] += r;
+        }
+        if (!(eta > 0.0)) {
+            c->has_state = false;
+            return fail(c, LB_E_DOMAIN, "eta = 1 - sum b rho <= 0 at some node");
+        }
+    }
+    for (int k = 0; k < N; ++k) mean[k] /= (double)c->n;
+    LB_CUDA(c, cudaMemcpyAsync(c->rho, rho, sizeof(double) * N * c->n, cudaMemcpyHostToDevice, c->stream));
+    if (mom)
+        LB_CUDA(c, cudaMemcpyAsync(c->mom, mom, sizeof(double) * N * c->D * c->n, cudaMemcpyHostToDevice, c->stream));
+    lb_status s = init_common(c, c->rho, mom ? c->mom : nullptr, mean);
+    if (s != LB_OK) return s;
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_init_fields_dev(lb_ctx *c, const double *rho_dev, const double *mom_dev) {
+    if (!c || !rho_dev) return LB_E_INVALID;
+    const int N = c->p.ncomp;
+    LB_CUDA(c, cudaSetDevice(c->p.device));
+    double mean[4] = {0, 0, 0, 0};
+    bool need_mean = false;
+    if (c->p.precision == LB_FP32_MIXED)
+        for (int k = 0; k < N; ++k) need_mean = need_mean || !(c->p.rho_ref[k] > 0.0);
+    if (need_mean) {
+        // mean densities through the diagnostics reduction (one synchronisation)
+        LB_CUDA(c, cudaMemcpyAsync(c->rho, rho_dev, sizeof(double) * N * c->n, cudaMemcpyDeviceToDevice, c->stream));
+        LB_CUDA(c, cudaMemsetAsync(c->mom, 0, sizeof(double) * N * c->D * c->n, c->stream));
+        FieldLaunch a = field_args(c);
+        cudaError_t e = run_field(c, 2, a);
+        if (e != cudaSuccess) return cuda_fail(c, e, "diag kernel");
+        c->launches += 2;
+        double h[7];
+        LB_CUDA(c, cudaMemcpyAsync(h, c->diag, sizeof(double) * (N + 3), cudaMemcpyDeviceToHost, c->stream));
+        LB_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (int k = 0; k < N; ++k) mean[k] = h[k] / (double)c->n;
+    }
+    return init_common(c, rho_dev, mom_dev, mean);
+}
+
+lb_status lb_step(lb_ctx *c, int64_t nsteps) {
+    lb_status s = usable(c);
+    if (s != LB_OK) return s;
+    if (nsteps < 0) return fail(c, LB_E_INVALID, "nsteps < 0");
+    for (int64_t t = 0; t < nsteps; ++t) {
+        cudaError_t e = run_step(c);
+        if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
+        c->cur ^= 1;
+        c->steps += 1;
+        c->launches += 1;
+        if (c->p.check_every > 0 && c->steps % c->p.check_every == 0) {
+            s = sync_check(c);
+            if (s != LB_OK) return s;
+        }
+    }
+    return LB_OK;
+}
+
+lb_status lb_read_moments_dev(lb_ctx *c, double *rho_dev, double *mom_dev) {
+    lb_status s = usable(c);
+    if (s != LB_OK) return s;
+    if (!rho_dev) return fail(c, LB_E_INVALID, "rho output is NULL");
+    FieldLaunch a = field_args(c);
+    a.rho_out = rho_dev;
+    a.mom_out = mom_dev;
+    cudaError_t e = run_field(c, 1, a);
+    if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel");
+    c->launches += 1;
+    return LB_OK;
+}
+
+lb_status lb_read_moments(lb_ctx *c, double *rho, double *mom) {
+    lb_status s = usable(c);
+    if (s != LB_OK) return s;
+    if (!rho) return fail(c, LB_E_INVALID, "rho output is NULL");
+    const int N = c->p.ncomp;
+    FieldLaunch a = field_args(c);
+    cudaError_t e = run_field(c, 1, a);
+    if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel");
+    c->launches += 1;
+    LB_CUDA(c, cudaMemcpyAsync(rho, c->rho, sizeof(double) * N * c->n, cudaMemcpyDeviceToHost, c->stream));
+    if (mom)
+        LB_CUDA(c, cudaMemcpyAsync(mom, c->mom, sizeof(double) * N * c->D * c->n, cudaMemcpyDeviceToHost, c->stream));
+    return sync_check(c);
+}
+
+lb_status lb_free_energy(lb_ctx *c, double *F, double *mass, double *mom_total) {
+    lb_status s = usable(c);
+    if (s != LB_OK) return s;
+    if (!F) return fail(c, LB_E_INVALID, "F output is NULL");
+    const int N = c->p.ncomp;
+    FieldLaunch a = field_args(c);
+    cudaError_t e = run_field(c, 1, a);
+    if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel");
+    e = run_field(c, 2, a);
+    if (e != cudaSuccess) return cuda_fail(c, e, "diag kernel");
+    c->launches += 3;
+    double h[7];
+    LB_CUDA(c, cudaMemcpyAsync(h, c->diag, sizeof(double) * (N + 3), cudaMemcpyDeviceToHost, c->stream));
+    s = sync_check(c);
+    if (s != LB_OK) return s;
+    *F = h[N];
+    if (mass)
+        for (int k = 0; k < N; ++k) mass[k] = h[k];
+    if (mom_total) {
+        mom_total[0] = h[N + 1];
+        mom_total[1] = c->D == 2 ? h[N + 2] : 0.0;
+    }
+    return LB_OK;
+}
+
+size_t lb_state_bytes(const lb_ctx *c) {
+    if (!c) return 0;
+    return sizeof(StateHeader) + c->elem * (size_t)c->p.ncomp * c->Q * c->n;
+}
+
+lb_status lb_save_state(lb_ctx *c, void *buf, size_t bytes) {
+    lb_status s = usable(c);
+    if (s != LB_OK) return s;
+    if (!buf || bytes < lb_state_bytes(c)) return fail(c, LB_E_INVALID, "state buffer too small");
+    StateHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, "LBVDWST1", 8);
+    h.abi = LBVDW_ABI;
+    h.lattice = (uint32_t)c->p.lattice;
+    h.nx = c->p.nx; h.ny = c->p.ny; h.ncomp = c->p.ncomp; h.precision = c->p.precision;
+    h.steps = c->steps;
+    h.hash = params_hash(c->p);
+    h.rho_ref_sum = 0.0;
+    for (int k = 0; k < 4; ++k) h.rho_ref_sum += c->dp.rho_ref[k] * (k + 1);
+    std::memcpy(buf, &h, sizeof h);
+    char *dst = static_cast<char *>(buf) + sizeof h;
+    LB_CUDA(c, cudaMemcpyAsync(dst, c->f[c->cur], lb_state_bytes(c) - sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    return sync_check(c);
+}
+
+lb_status lb_load_state(lb_ctx *c, const void *buf, size_t bytes) {
+    if (!c || !buf || bytes < lb_state_bytes(c)) return LB_E_INVALID;
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof h);
+    if (std::memcmp(h.magic, "LBVDWST1", 8) != 0 || h.abi != LBVDW_ABI || h.lattice != (uint32_t)c->p.lattice ||
+        h.nx != c->p.nx || h.ny != c->p.ny || h.ncomp != c->p.ncomp || h.precision != c->p.precision ||
+        h.hash != params_hash(c->p))
+        return fail(c, LB_E_INVALID, "saved state does not match this context");
+    LB_CUDA(c, cudaSetDevice(c->p.device));
+    if (c->p.precision == LB_FP32_MIXED) {
+        double sum = 0.0;
+        for (int k = 0; k < 4; ++k) sum += c->dp.rho_ref[k] * (k + 1);
+        if (!c->has_state || sum != h.rho_ref_sum)
+            return fail(c, LB_E_INVALID, "mixed-precision state needs the same reference densities (init first)");
+    }
+    const char *src = static_cast<const char *>(buf) + sizeof h;
+    c->cur = 0;
+    LB_CUDA(c, cudaMemcpyAsync(c->f[0], src, lb_state_bytes(c) - sizeof h, cudaMemcpyHostToDevice, c->stream));
+    LB_CUDA(c, cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->steps = h.steps;
+    c->has_state = true;
+    c->poisoned = false;
+    c->msg.clear();
+    return LB_OK;
+}
+
+int64_t lb_step_count(const lb_ctx *c) { return c ? c->steps : -1; }
+
+int64_t lb_launch_count(const lb_ctx *c) { return c ? c->launches : -1; }
+
+lb_status lb_destroy(lb_ctx *c) {
+    if (!c) return LB_OK;
+    cudaSetDevice(c->p.device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(c->f[0]);
+    cudaFree(c->f[1]);
+    cudaFree(c->rho);
+    cudaFree(c->mom);
+    cudaFree(c->partial);
+    cudaFree(c->diag);
+    cudaFree(c->err);
+    delete c;
+    return LB_OK;
+}
+
+const char *lb_status_str(lb_status s) {
+    int k = (int)s;
+    return (k >= 0 && k <= 6) ? k_status[k] : "LB_E_UNKNOWN";
+}
+
+const char *lb_last_error(const lb_ctx *c) {
+    if (!c) return "NULL context";
+    return c->msg.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,6 @@
+// D1Q3 lattice, FP64 populations and arithmetic.
+#define LBVDW_LAT 1
+#define LBVDW_S double
+#define LBVDW_R double
+#define LBVDW_NAME d1q3_f64
+#include "lb_tu.cuh"

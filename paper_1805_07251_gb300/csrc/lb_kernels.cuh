@@ -1,0 +1,460 @@
+// lb_kernels.cuh -- device code of the fused multicomponent van der Waals
+// lattice Boltzmann timestep (Ridl & Wagner, arXiv:1805.07251, Sec. III and V).
+//
+// One CTA owns a TX x TY tile of nodes.  A timestep is one launch:
+//   phase 1  densities rho^c on the tile plus a 2-node ring        (Sec. III moments)
+//   phase 2  mu^c on the tile plus a 1-node ring, FP64            (Eq. discreteChemicalPotential)
+//   phase 3  per node: force (Eq. forceMuLog / forceMuId), friction (Eq. forceFriction),
+//            Psi (Eq. forceCorrectionsPsi), BGK + forcing (Eqs. feq, BGKcollisionOperator),
+//            push-streaming to the other buffer (Eq. LBequation).
+// rho and mu live only in shared memory; HBM sees one read and one write of
+// every population per step (plus halo re-reads that the L2 serves).
+//
+// Storage type S holds the deviation g_i^c = f_i^c - w_i rho_ref^c (rho_ref = 0 in the
+// FP64 path, so g = f there).  Compute type R is double in the FP64 path and float in
+// the mixed path; mu^c, eta, 1/eta and the logs are always double.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbvdw {
+
+constexpr unsigned ERR_DOMAIN = 1u;   // rho^c <= 0, eta <= 0 or non-finite value
+
+struct DevParams {
+    int nx, ny;
+    double omega;      // 1 / tau
+    double psi_g;      // (tau - 1/4) / tau : coefficient of G G / rho in -Psi
+    double psi_l;      // 1 / (12 tau)      : coefficient of Lap rho in -Psi
+    double kT, gamma;
+    double a[16], kappa[16], lam[16];  // stride 4
+    double b[4];
+    double rho_ref[4];
+    unsigned *err;     // error word (device)
+};
+
+// ---------------------------------------------------------------------------
+// lattices.  D1Q3: v = 0, +1, -1 (Sec. V), w = 2/3, 1/6, 1/6 (the weights of the
+// explicit D1Q3 update at theta = 1/3).  D2Q9: rest, E, N, W, S, NE, NW, SW, SE.
+// ---------------------------------------------------------------------------
+template <int LAT> struct Lat;
+template <> struct Lat<1> {
+    static constexpr int Q = 3, D = 1, HY = 0;
+    __host__ __device__ static constexpr int vx(int i) { return i == 1 ? 1 : (i == 2 ? -1 : 0); }
+    __host__ __device__ static constexpr int vy(int) { return 0; }
+    __host__ __device__ static constexpr double w(int i) { return i == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+};
+template <> struct Lat<2> {
+    static constexpr int Q = 9, D = 2, HY = 1;
+    __host__ __device__ static constexpr int vx(int i) {
+        return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int vy(int i) {
+        return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+};
+
+__device__ __forceinline__ int wrap(int g, int n) {
+    g %= n;
+    return g < 0 ? g + n : g;
+}
+
+__device__ __forceinline__ size_t pop_index(int c, int i, int Q, int y, int x, int nx, int ny) {
+    return ((size_t)(c * Q + i) * (size_t)ny + (size_t)y) * (size_t)nx + (size_t)x;
+}
+
+// Stencils on a shared-memory array with row length EXW.
+// D1Q3: central difference (phi+ - phi-)/2 and Lap = phi+ + phi- - 2 phi (Sec. V).
+// D2Q9: D = (1/theta) sum w_i v_i phi_i, Lap = (2/theta) sum w_i (phi_i - phi_0).
+template <int LAT, class T>
+__device__ __forceinline__ void grad_at(const T *s, int ex, int ey, int EXW, T &gx, T &gy) {
+    const T *p = s + ey * EXW + ex;
+    if constexpr (LAT == 1) {
+        gx = (T)0.5 * (p[1] - p[-1]);
+        gy = (T)0;
+    } else {
+        T e = p[1], wv = p[-1], n = p[EXW], sv = p[-EXW];
+        T ne = p[EXW + 1], nw = p[EXW - 1], sw = p[-EXW - 1], se = p[-EXW + 1];
+        gx = (e - wv) * (T)(1.0 / 3.0) + ((ne + se) - (nw + sw)) * (T)(1.0 / 12.0);
+        gy = (n - sv) * (T)(1.0 / 3.0) + ((ne + nw) - (se + sw)) * (T)(1.0 / 12.0);
+    }
+}
+
+template <int LAT, class T>
+__device__ __forceinline__ T lap_at(const T *s, int ex, int ey, int EXW) {
+    const T *p = s + ey * EXW + ex;
+    if constexpr (LAT == 1) {
+        return (p[1] + p[-1]) - (T)2 * p[0];
+    } else {
+        T axis = (p[1] + p[-1]) + (p[EXW] + p[-EXW]);
+        T diag = (p[EXW + 1] + p[EXW - 1]) + (p[-EXW + 1] + p[-EXW - 1]);
+        return axis * (T)(2.0 / 3.0) + diag * (T)(1.0 / 6.0) - p[0] * (T)(10.0 / 3.0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the fused step
+// ---------------------------------------------------------------------------
+template <int LAT, int N, int TX, int TY, class S, class R, int FORCE>
+__global__ void __launch_bounds__(TX *TY)
+    lb_step_kernel(const S *__restrict__ fin, S *__restrict__ fout, DevParams P) {
+    using L = Lat<LAT>;
+    constexpr int Q = L::Q;
+    constexpr int HY = L::HY;
+    constexpr int EX = TX + 4, EY = TY + 4 * HY;  // densities: tile + 2 ring
+    constexpr int MX = TX + 2, MY = TY + 2 * HY;  // mu: tile + 1 ring
+    constexpr int NT = TX * TY;
+
+    __shared__ double s_rho[N][EY * EX];
+    __shared__ double s_phi[N][MY * MX];  // gamma mu (log) or gamma mu - theta ln rho (nid)
+
+    const int nx = P.nx, ny = P.ny;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int tid = threadIdx.x + TX * threadIdx.y;
+
+    // ---- phase 1: rho^c on tile + 2 ring ------------------------------------
+    for (int k = tid; k < EX * EY; k += NT) {
+        int ex = k % EX, ey = k / EX;
+        int gx = wrap(x0 + ex - 2, nx);
+        int gy = (LAT == 1) ? 0 : wrap(y0 + ey - 2, ny);
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            R acc = (R)0;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) acc += (R)fin[pop_index(c, i, Q, gy, gx, nx, ny)];
+            s_rho[c][k] = P.rho_ref[c] + (double)acc;
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 2: mu^c (FP64) on tile + 1 ring --------------------------------
+    unsigned bad = 0;
+    for (int k = tid; k < MX * MY; k += NT) {
+        int mx = k % MX, my = k / MX;
+        int ex = mx + 1, ey = my + HY;
+        double r[N], lp[N];
+        double eta = 1.0, rt = 0.0;
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            r[c] = s_rho[c][ey * EX + ex];
+            lp[c] = lap_at<LAT, double>(s_rho[c], ex, ey, EX);
+            eta -= P.b[c] * r[c];
+            rt += r[c];
+        }
+        bool ok = eta > 0.0;
+#pragma unroll
+        for (int c = 0; c < N; ++c) ok = ok && (r[c] > 0.0);
+        if (!ok) bad = 1;
+        double ieta = 1.0 / eta;
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            double m = P.kT * (log(r[c] * ieta) + P.b[c] * rt * ieta);
+#pragma unroll
+            for (int cc = 0; cc < N; ++cc) m -= 2.0 * P.a[c * 4 + cc] * r[cc] + P.kappa[c * 4 + cc] * lp[cc];
+            double ph = P.gamma * m;
+            if constexpr (FORCE == 1) ph -= (1.0 / 3.0) * log(r[c]);
+            s_phi[c][k] = ph;
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 3: forces, collision, streaming --------------------------------
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x = x0 + tx, y = y0 + ty;
+    if (x >= nx || y >= ny) {
+        if (bad) atomicOr(P.err, ERR_DOMAIN);
+        return;
+    }
+    const int ex = tx + 2, ey = ty + 2 * HY;
+    const int mx = tx + 1, my = ty + HY;
+
+    R rho[N], ux[N], uy[N], Gx[N], Gy[N], lap[N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        double rd = s_rho[c][ey * EX + ex];
+        rho[c] = (R)rd;
+        lap[c] = (R)lap_at<LAT, double>(s_rho[c], ex, ey, EX);
+        double gpx, gpy;
+        grad_at<LAT, double>(s_phi[c], mx, my, MX, gpx, gpy);
+        double gmx, gmy;
+        if constexpr (FORCE == 0) {
+            double grx, gry;
+            grad_at<LAT, double>(s_rho[c], ex, ey, EX, grx, gry);
+            gmx = -rd * gpx + (1.0 / 3.0) * grx;
+            gmy = -rd * gpy + (1.0 / 3.0) * gry;
+        } else {
+            gmx = -rd * gpx;
+            gmy = -rd * gpy;
+        }
+        Gx[c] = (R)gmx;
+        Gy[c] = (R)gmy;
+        // bare momentum of this node
+        R jx = (R)0, jy = (R)0;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            R g = (R)fin[pop_index(c, i, Q, y, x, nx, ny)];
+            if (L::vx(i) == 1) jx += g;
+            if (L::vx(i) == -1) jx -= g;
+            if (L::vy(i) == 1) jy += g;
+            if (L::vy(i) == -1) jy -= g;
+        }
+        R ir = (R)1 / rho[c];
+        ux[c] = jx * ir;
+        uy[c] = jy * ir;
+    }
+
+    // friction with the implicit u-hat: (D + L/2) h = -L u0, G^f = D h  (per direction)
+    if constexpr (N > 1) {
+        R W[N][N];
+#pragma unroll
+        for (int c = 0; c < N; ++c)
+#pragma unroll
+            for (int cc = 0; cc < N; ++cc)
+                W[c][cc] = (c == cc) ? (R)0 : (R)P.lam[c * 4 + cc] * rho[c] * rho[cc] / (rho[c] + rho[cc]);
+#pragma unroll
+        for (int d = 0; d < L::D; ++d) {
+            R u0[N], M[N][N], h[N];
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                R uu = d == 0 ? ux[c] : uy[c];
+                R gg = d == 0 ? Gx[c] : Gy[c];
+                u0[c] = uu + gg / ((R)2 * rho[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                R diag = rho[c], rhs = (R)0;
+#pragma unroll
+                for (int cc = 0; cc < N; ++cc) {
+                    M[c][cc] = (R)(-0.5) * W[c][cc];
+                    diag += (R)0.5 * W[c][cc];
+                    rhs -= W[c][cc] * (u0[c] - u0[cc]);
+                }
+                M[c][c] = diag;
+                h[c] = rhs;
+            }
+            // symmetric positive definite: elimination without pivoting
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                R inv = (R)1 / M[k][k];
+#pragma unroll
+                for (int r2 = k + 1; r2 < N; ++r2) {
+                    R m = M[r2][k] * inv;
+#pragma unroll
+                    for (int c2 = k + 1; c2 < N; ++c2) M[r2][c2] -= m * M[k][c2];
+                    h[r2] -= m * h[k];
+                }
+            }
+#pragma unroll
+            for (int k = N - 1; k >= 0; --k) {
+                R s = h[k];
+#pragma unroll
+                for (int c2 = k + 1; c2 < N; ++c2) s -= M[k][c2] * h[c2];
+                h[k] = s / M[k][k];
+            }
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                if (d == 0) Gx[c] += rho[c] * h[c];
+                else Gy[c] += rho[c] * h[c];
+            }
+        }
+    }
+
+    const R omega = (R)P.omega, cg = (R)P.psi_g, cl = (R)P.psi_l;
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        const R r = rho[c], u = ux[c], v = uy[c], gx = Gx[c], gy = Gy[c];
+        const R ir = (R)1 / r;
+        // second forcing moment S = G u + u G - Psi, -Psi = cg G G / rho + cl Lap rho I
+        const R Sxx = (R)2 * gx * u + cg * gx * gx * ir + cl * lap[c];
+        const R Syy = (R)2 * gy * v + cg * gy * gy * ir + cl * lap[c];
+        const R Sxy = gx * v + u * gy + cg * gx * gy * ir;
+        const R usq = u * u + v * v;
+        const R drho = (R)((double)s_rho[c][ey * EX + ex] - P.rho_ref[c]);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            constexpr R third = (R)(1.0 / 3.0);
+            const int cx = L::vx(i), cy = L::vy(i);
+            const R wi = (R)L::w(i);
+            const R vu = (R)cx * u + (R)cy * v;
+            const R vG = (R)cx * gx + (R)cy * gy;
+            // f^eq_i - w_i rho_ref = w_i (rho - rho_ref) + w_i rho (3 v.u + 4.5 (v.u)^2 - 1.5 u^2)
+            const R feq_dev = wi * drho + wi * r * ((R)3 * vu + (R)4.5 * vu * vu - (R)1.5 * usq);
+            R SQ = Sxx * ((R)(cx * cx) - third);
+            if constexpr (LAT == 2) SQ += Syy * ((R)(cy * cy) - third) + (R)2 * Sxy * (R)(cx * cy);
+            const R Fi = wi * ((R)3 * vG + (R)4.5 * SQ);
+            const R g = (R)fin[pop_index(c, i, Q, y, x, nx, ny)];
+            const R post = g + omega * (feq_dev - g) + Fi;
+            const int dx = (LAT == 1) ? wrap(x + cx, nx) : wrap(x + cx, nx);
+            const int dy = (LAT == 1) ? 0 : wrap(y + cy, ny);
+            fout[pop_index(c, i, Q, dy, dx, nx, ny)] = (S)post;
+        }
+    }
+    if (bad) atomicOr(P.err, ERR_DOMAIN);
+}
+
+// ---------------------------------------------------------------------------
+// equilibrium initialisation (Eq. feq at theta = 1/3), stored as deviations
+// ---------------------------------------------------------------------------
+template <int LAT, int N, class S>
+__global__ void lb_init_kernel(S *__restrict__ f, const double *__restrict__ rho,
+                               const double *__restrict__ mom, DevParams P) {
+    using L = Lat<LAT>;
+    constexpr int Q = L::Q, D = L::D;
+    const size_t n = (size_t)P.nx * P.ny;
+    for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < n; s += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(s % P.nx), y = (int)(s / P.nx);
+        double eta = 1.0;
+        bool ok = true;
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            double r = rho[c * n + s];
+            eta -= P.b[c] * r;
+            ok = ok && (r > 0.0) && isfinite(r);
+        }
+        if (!(ok && eta > 0.0)) atomicOr(P.err, ERR_DOMAIN);
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            double r = rho[c * n + s];
+            double u = 0.0, v = 0.0;
+            if (mom) {
+                u = mom[(c * D + 0) * n + s] / r;
+                if (D == 2) v = mom[(c * D + 1) * n + s] / r;
+            }
+            double usq = u * u + v * v;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                double vu = L::vx(i) * u + L::vy(i) * v;
+                double wi = L::w(i);
+                double dev = wi * (r - P.rho_ref[c]) + wi * r * (3.0 * vu + 4.5 * vu * vu - 1.5 * usq);
+                f[pop_index(c, i, Q, y, x, P.nx, P.ny)] = (S)dev;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// moments rho^c, j^c (FP64 out) of the stored state
+// ---------------------------------------------------------------------------
+template <int LAT, int N, class S>
+__global__ void lb_moments_kernel(const S *__restrict__ f, double *__restrict__ rho,
+                                  double *__restrict__ mom, DevParams P) {
+    using L = Lat<LAT>;
+    constexpr int Q = L::Q, D = L::D;
+    const size_t n = (size_t)P.nx * P.ny;
+    for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < n; s += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(s % P.nx), y = (int)(s / P.nx);
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            double r = 0.0, jx = 0.0, jy = 0.0;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                double g = (double)f[pop_index(c, i, Q, y, x, P.nx, P.ny)];
+                r += g;
+                jx += L::vx(i) * g;
+                jy += L::vy(i) * g;
+            }
+            rho[c * n + s] = P.rho_ref[c] + r;
+            if (mom) {
+                mom[(c * D + 0) * n + s] = jx;
+                if (D == 2) mom[(c * D + 1) * n + s] = jy;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// diagnostics: per-CTA partials of [mass_0..mass_{N-1}, F, jx, jy] in FP64
+// (fixed per-thread order, fixed shuffle tree), then one CTA sums the partials
+// in index order.  Also flags rho <= 0, eta <= 0 and non-finite values.
+// ---------------------------------------------------------------------------
+constexpr int DIAG_THREADS = 256;
+
+template <int V>
+__device__ __forceinline__ void block_sum(double (&v)[V], double *out) {
+    __shared__ double s_part[DIAG_THREADS / 32][V];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < V; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < V; ++k) s_part[wid][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            double acc = 0.0;
+            for (int w = 0; w < DIAG_THREADS / 32; ++w) acc += s_part[w][k];
+            out[k] = acc;
+        }
+    }
+}
+
+template <int LAT, int N>
+__global__ void __launch_bounds__(DIAG_THREADS)
+    lb_diag_partial_kernel(const double *__restrict__ rho, const double *__restrict__ mom,
+                           double *__restrict__ partial, DevParams P) {
+    using L = Lat<LAT>;
+    constexpr int D = L::D;
+    constexpr int V = N + 3;
+    const size_t n = (size_t)P.nx * P.ny;
+    double acc[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) acc[k] = 0.0;
+    for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < n; s += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(s % P.nx), y = (int)(s / P.nx);
+        double r[N], lp[N], eta = 1.0;
+        bool ok = true;
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            const double *rc = rho + c * n;
+            r[c] = rc[s];
+            double e = rc[(size_t)y * P.nx + wrap(x + 1, P.nx)], wv = rc[(size_t)y * P.nx + wrap(x - 1, P.nx)];
+            if constexpr (LAT == 1) {
+                lp[c] = (e + wv) - 2.0 * r[c];
+            } else {
+                int yn = wrap(y + 1, P.ny), ys = wrap(y - 1, P.ny);
+                int xe = wrap(x + 1, P.nx), xw = wrap(x - 1, P.nx);
+                double nn = rc[(size_t)yn * P.nx + x], ss = rc[(size_t)ys * P.nx + x];
+                double ne = rc[(size_t)yn * P.nx + xe], nw = rc[(size_t)yn * P.nx + xw];
+                double se = rc[(size_t)ys * P.nx + xe], sw = rc[(size_t)ys * P.nx + xw];
+                lp[c] = ((e + wv) + (nn + ss)) * (2.0 / 3.0) + ((ne + nw) + (se + sw)) * (1.0 / 6.0) -
+                        r[c] * (10.0 / 3.0);
+            }
+            eta -= P.b[c] * r[c];
+            ok = ok && (r[c] > 0.0) && isfinite(r[c]);
+        }
+        ok = ok && eta > 0.0;
+        if (!ok) atomicOr(P.err, ERR_DOMAIN);
+        double F = 0.0;
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            acc[c] += r[c];
+            F += P.kT * r[c] * log(r[c] / eta);
+#pragma unroll
+            for (int cc = 0; cc < N; ++cc) F -= P.a[c * 4 + cc] * r[c] * r[cc] + 0.5 * P.kappa[c * 4 + cc] * r[c] * lp[cc];
+            acc[N + 1] += mom[(c * D + 0) * n + s];
+            if (D == 2) acc[N + 2] += mom[(c * D + 1) * n + s];
+        }
+        acc[N] += F;
+    }
+    block_sum<V>(acc, partial + (size_t)blockIdx.x * V);
+}
+
+template <int V>
+__global__ void __launch_bounds__(DIAG_THREADS)
+    lb_diag_final_kernel(const double *__restrict__ partial, int nparts, double *__restrict__ out) {
+    double acc[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) acc[k] = 0.0;
+    for (int p = threadIdx.x; p < nparts; p += DIAG_THREADS)
+#pragma unroll
+        for (int k = 0; k < V; ++k) acc[k] += partial[(size_t)p * V + k];
+    block_sum<V>(acc, out);
+}
+
+}  // namespace lbvdw

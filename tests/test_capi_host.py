@@ -1,0 +1,81 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads and
+exports every function that include/lbvdw.h declares, and the pure-host entry
+points behave as documented."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lbvdw.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(lb_[a-z0-9_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1805_07251_gb300 import build, capi
+
+    build.build()
+    return capi.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lb_create", "lb_init_fields", "lb_step", "lb_read_moments", "lb_free_energy",
+                     "lb_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1805_07251_gb300 import capi
+
+    out = subprocess.run(["nm", "-D", "--defined-only", capi.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT\s+(lb_[a-z0-9_]+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        assert hasattr(lib, n)
+
+
+def test_status_strings_and_defaults(lib):
+    from paper_1805_07251_gb300 import capi
+
+    assert capi.status_str(capi.LB_OK) == "LB_OK"
+    assert capi.status_str(capi.LB_E_DOMAIN) == "LB_E_DOMAIN"
+    assert capi.status_str(99) == "LB_E_UNKNOWN"
+    p = capi.lb_default_params()
+    assert p.abi == capi.LBVDW_ABI and p.tau == 1.0 and p.ncomp == 2 and p.lattice == capi.LB_D2Q9
+    assert ctypes.sizeof(capi.lb_params) == 8 * 4 + 8 * 3 + 8 * (16 * 3 + 8) + 4 * 4 + 8
+
+
+def test_null_arguments_are_rejected_without_cuda(lib):
+    from paper_1805_07251_gb300 import capi
+
+    assert lib.lb_create(None, None) == capi.LB_E_INVALID
+    assert lib.lb_step(None, 1) == capi.LB_E_INVALID
+    assert lib.lb_destroy(None) == capi.LB_OK
+    assert lib.lb_last_error(None) == b"NULL context"
+    # invalid parameter sets fail validation before any CUDA call
+    p = capi.lb_default_params()
+    out = ctypes.c_void_p()
+    assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID  # b = 0
+    p.b[0] = p.b[1] = 0.3
+    p.a[1], p.a[4] = 0.5, 0.4                                                  # a not symmetric
+    assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID
+    p.a[4] = 0.5
+    p.tau = 0.5
+    assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID
+    p.tau = 1.0
+    p.ncomp = 5
+    assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID
+    p.ncomp = 2
+    p.lattice = capi.LB_D1Q3  # ny must be 1
+    assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID
