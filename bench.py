@@ -9,10 +9,12 @@ is one lattice Boltzmann timestep (one fused kernel launch) of the whole
 lattice; the L2 is flushed (256 MB write) between timed steps, outside the
 timed events.
 
-Metric: component-MLUPS = ncomp * nodes * steps / s / 1e6, for the FP32-mixed
-path (headline ``value``) with the FP64 path measured in the same run
-(``fp64``), plus the roofline fraction of the step kernel against the measured
-HBM copy bandwidth.
+Metric: component-MLUPS = ncomp * nodes * steps / s / 1e6.  Three paths are
+timed in the same run: FP32 storage with the chemical potential in
+double-float arithmetic (headline ``value``), FP32 storage with the chemical
+potential in FP64 (``fp32_fp64mu``) and the plain FP64 path (``fp64``), each
+with the roofline fraction of its step kernel against the measured HBM copy
+bandwidth.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -38,6 +40,8 @@ METRIC = "component-MLUPS"
 UNIT = "component-MLUPS"
 WORKLOAD = "c2"
 FLUSH_BYTES = 256 << 20
+DTYPES = {"fp32_dfmu": "f32 (populations and step), double-float mu",
+          "fp32_mixed": "f32 (populations and step), f64 mu", "fp64": "f64"}
 
 
 def parse():
@@ -48,6 +52,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--only", choices=["fp32_dfmu", "fp32_mixed", "fp64"], default=None,
+                    help="time one path only (profiling runs): no e2e, no cpu baseline")
     return ap.parse_args()
 
 
@@ -219,9 +225,13 @@ def main():
 
     results = {}
     clocks = None
-    for precision in (["fp32_mixed"] if args.no_fp64 else ["fp32_mixed", "fp64"]):
+    HEAD = args.only or "fp32_dfmu"
+    paths = [HEAD, "fp32_mixed"] if args.no_fp64 else [HEAD, "fp32_mixed", "fp64"]
+    if args.only:
+        paths = [args.only]
+    for precision in paths:
         sim, ev, l0, stream = time_path(torch, Simulation, kw, rho, precision, args.steps, args.warmup, flush, dev)
-        sampler = ClockSampler(dev) if precision == "fp32_mixed" else None
+        sampler = ClockSampler(dev) if precision == HEAD else None
         if sampler:
             sampler.start()
         if dist is not None:
@@ -246,71 +256,76 @@ def main():
             total_ms = float(t.item())
         ms = total_ms / args.steps
         value = world * N * nodes * args.steps / (total_ms * 1e-3) / 1e6
-        elem = 4 if precision == "fp32_mixed" else 8
+        elem = 8 if precision == "fp64" else 4
         alg_bytes = N * nodes * 9 * 2 * elem
         achieved = alg_bytes / (ms * 1e-3) / 1e9
         results[precision] = dict(value=value, ms=ms, launches=launches, alg_bytes=alg_bytes, achieved=achieved)
         sim.close()
 
-    # end to end through the C ABI with host buffers: pinned host densities in,
-    # K timesteps, densities and momenta back to pinned host memory
-    sim = Simulation(precision="fp32_mixed", device=dev, stream=torch.cuda.current_stream(dev).cuda_stream, **kw)
-    h_rho = torch.from_numpy(rho).pin_memory().numpy()
-    o_rho = torch.empty(rho.shape, dtype=torch.float64).pin_memory().numpy()
-    o_mom = torch.empty((N, 2) + rho.shape[1:], dtype=torch.float64).pin_memory().numpy()
-    from paper_1805_07251_gb300 import capi
+    e2e = None
+    if not args.only:
+        # end to end through the C ABI with host buffers: pinned host densities in,
+        # K timesteps, densities and momenta back to pinned host memory
+        sim = Simulation(precision=HEAD, device=dev, stream=torch.cuda.current_stream(dev).cuda_stream, **kw)
+        h_rho = torch.from_numpy(rho).pin_memory().numpy()
+        o_rho = torch.empty(rho.shape, dtype=torch.float64).pin_memory().numpy()
+        o_mom = torch.empty((N, 2) + rho.shape[1:], dtype=torch.float64).pin_memory().numpy()
+        from paper_1805_07251_gb300 import capi
 
-    sim.init(h_rho)
-    sim.step(args.warmup)
-    capi.lb_read_moments(sim.ctx, o_rho, o_mom)
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    capi.lb_init_fields(sim.ctx, h_rho)
-    sim.step(args.steps)
-    capi.lb_read_moments(sim.ctx, o_rho, o_mom)
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    sim.close()
-    e2e = {"value": world * N * nodes * args.steps / e2e_s / 1e6, "unit": UNIT,
-           "h2d_bytes_per_step": int(rho.nbytes // args.steps),
-           "d2h_bytes_per_step": int((o_rho.nbytes + o_mom.nbytes) // args.steps),
-           "note": "per-step bytes amortise one host->device field upload and one device->host "
-                   "read of densities and momenta over the K timesteps of the job"}
+        sim.init(h_rho)
+        sim.step(args.warmup)
+        capi.lb_read_moments(sim.ctx, o_rho, o_mom)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        capi.lb_init_fields(sim.ctx, h_rho)
+        sim.step(args.steps)
+        capi.lb_read_moments(sim.ctx, o_rho, o_mom)
+        e2e_s = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        sim.close()
+        e2e = {"value": world * N * nodes * args.steps / e2e_s / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(rho.nbytes // args.steps),
+               "d2h_bytes_per_step": int((o_rho.nbytes + o_mom.nbytes) // args.steps),
+               "note": "per-step bytes amortise one host->device field upload and one device->host "
+                       "read of densities and momenta over the K timesteps of the job"}
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
 
-    head = results["fp32_mixed"]
+    head = results[HEAD]
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 populations, f64 mu", "data": "synthetic",
-        "config": {"workload": "D2Q9, 2 components, 1024x1024 periodic, spinodal mixture (c2), FP32-mixed",
+        "vs_baseline": None, "dtype": DTYPES[HEAD], "data": "synthetic",
+        "config": {"workload": "D2Q9, 2 components, 1024x1024 periodic, spinodal mixture (c2), " + HEAD,
                    "nodes": nodes, "ncomp": N, "tile": "32x8", "l2": "flushed between steps (256 MB write)",
                    "parallelism": "independent replica per GPU" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": head["achieved"], "peak": peak_gbs, "unit": "GB/s",
                      "frac": head["achieved"] / peak_gbs, "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "lb_step_kernel<D2Q9, N=2, 32x8, float>",
+                     "kernel": "lb_step_kernel<D2Q9, N=2, 32x8, %s>" % HEAD,
                      "alg_bytes_per_launch": head["alg_bytes"]},
         "gpu_launches": head["launches"],
-        "e2e": e2e,
     }
-    if "fp64" in results:
-        r64 = results["fp64"]
-        line["fp64"] = {"value": r64["value"], "unit": UNIT, "ms_per_step": r64["ms"],
-                        "roofline_hbm": {"achieved": r64["achieved"], "peak": peak_gbs, "unit": "GB/s",
-                                         "frac": r64["achieved"] / peak_gbs}}
-        line["gpu_launches"] += r64["launches"]
+    if e2e is not None:
+        line["e2e"] = e2e
+    for key, name in (("fp32_mixed", "fp32_fp64mu"), ("fp64", "fp64")):
+        if key not in results or key == HEAD:
+            continue
+        rr = results[key]
+        line[name] = {"value": rr["value"], "unit": UNIT, "ms_per_step": rr["ms"], "dtype": DTYPES[key],
+                      "roofline_hbm": {"achieved": rr["achieved"], "peak": peak_gbs, "unit": "GB/s",
+                                       "frac": rr["achieved"] / peak_gbs}}
+        line["gpu_launches"] += rr["launches"]
     if clocks:
         line["clocks"] = clocks
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and not args.only:
         ncb = 256
         steps_cb = 100
         v, dt = cpu_baseline_oracle(kw, rho, ncb, steps_cb)

@@ -69,9 +69,13 @@ typedef enum {
 typedef enum { LB_D1Q3 = 1, LB_D2Q9 = 2 } lb_lattice;
 
 typedef enum {
-    LB_FP64 = 0,      /* populations and all arithmetic in FP64 */
-    LB_FP32_MIXED = 1 /* FP32 populations stored as deviations f_i - w_i rho_ref^c,
-                         FP64 in mu^c (eta, 1/eta, logs) and in mass sums */
+    LB_FP64 = 0,       /* populations and all arithmetic in FP64 */
+    LB_FP32_MIXED = 1, /* FP32 populations stored as deviations f_i - w_i rho_ref^c;
+                          FP64 in mu^c (eta, 1/eta, the logarithms -- a table-driven FP64
+                          log -- and the differences of mu) and in mass sums */
+    LB_FP32_DFMU = 2   /* as LB_FP32_MIXED, with the FP64 operations of mu^c done in
+                          double-float (pairs of FP32, ~44 significant bits) on the FP32
+                          pipe; mass sums stay FP64 */
 } lb_precision;
 
 typedef enum { LB_FORCE_LOG = 0, LB_FORCE_NID = 1 } lb_force_method;
@@ -93,11 +97,12 @@ typedef struct {
     double lambda[16];   /* friction lambda^{cc'} (Eq. forceFriction), stride 4, symmetric,
                             >= 0; diagonal ignored */
     double b[4];         /* excluded volume b^c > 0 */
-    double rho_ref[4];   /* LB_FP32_MIXED only: reference density of component c whose
+    double rho_ref[4];   /* FP32 storage only: reference density of component c whose
                             rest equilibrium is subtracted before FP32 storage; 0 = use
                             the mean density set by lb_init_fields */
     int32_t device;      /* CUDA device ordinal */
-    int32_t tile_x, tile_y; /* 0 = library default / autotuned choice */
+    int32_t tile_x, tile_y; /* 0 = default; D2Q9: 32x8, 64x4, 32x16 or 64x8;
+                               D1Q3: 128x1 or 256x1 */
     void *stream;        /* cudaStream_t for every launch and copy; NULL = legacy default */
 } lb_params;
 

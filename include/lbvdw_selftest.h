@@ -1,0 +1,34 @@
+/*
+ * lbvdw_selftest.h -- self-test entry point of the lbvdw library (not part of the
+ * lattice Boltzmann step).  It exposes the two logarithms the chemical-potential
+ * stage uses on GB300 so that tests can compare them with CUDA's double-precision
+ * log on the same device:
+ *   - the table-driven FP64 logarithm of the LB_FP32_MIXED path;
+ *   - the double-float logarithm of the LB_FP32_DFMU path.
+ * The chemical potential that needs these logarithms is Eq. discreteChemicalPotential
+ * of Ridl & Wagner (arXiv:1805.07251), mu^c = kT ln(rho^c/eta) + ...
+ */
+#ifndef LBVDW_SELFTEST_H
+#define LBVDW_SELFTEST_H
+
+#include "lbvdw.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* For n host values x[k] > 0 (normal, finite) compute on device `device`:
+ *   out_tbl[k] = table-driven FP64 log(x[k]),
+ *   out_df[k]  = double-float log of x[k] (x first rounded to a double-float pair),
+ *                returned as hi + lo in double,
+ *   out_ref[k] = CUDA's double-precision log(x[k]).
+ * All arrays are host arrays of n doubles owned by the caller.  Allocates and frees
+ * its own device scratch; synchronous.  Errors: LB_E_INVALID (NULL pointer, n < 1),
+ * LB_E_NOMEM, LB_E_CUDA. */
+lb_status lb_selftest_log(int32_t device, const double *x, int64_t n, double *out_tbl, double *out_df,
+                          double *out_ref);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBVDW_SELFTEST_H */

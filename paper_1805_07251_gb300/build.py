@@ -40,7 +40,7 @@ def _sources():
 
 def _digest():
     h = hashlib.sha256()
-    files = _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "lbvdw.h")]
+    files = _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(glob.glob(os.path.join(INCLUDE, "*.h")))
     for f in files:
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())

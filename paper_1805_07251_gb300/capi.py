@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "liblbvdw.so")
 LBVDW_ABI = 1
 LB_OK, LB_E_INVALID, LB_E_NOMEM, LB_E_CUDA, LB_E_DOMAIN, LB_E_TIMEOUT, LB_E_STATE = range(7)
 LB_D1Q3, LB_D2Q9 = 1, 2
-LB_FP64, LB_FP32_MIXED = 0, 1
+LB_FP64, LB_FP32_MIXED, LB_FP32_DFMU = 0, 1, 2
 LB_FORCE_LOG, LB_FORCE_NID = 0, 1
 
 
@@ -86,6 +86,7 @@ def load():
         "lb_destroy": (ctypes.c_int, [C]),
         "lb_status_str": (ctypes.c_char_p, [ctypes.c_int]),
         "lb_last_error": (ctypes.c_char_p, [C]),
+        "lb_selftest_log": (ctypes.c_int, [ctypes.c_int32, _DP, ctypes.c_int64, _DP, _DP, _DP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -188,3 +189,13 @@ def lb_destroy(ctx):
 
 def lb_last_error(ctx):
     return load().lb_last_error(ctx).decode()
+
+
+def lb_selftest_log(device, x):
+    """Table-driven FP64 log, double-float log and CUDA's log of x on the device."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    o = [np.empty_like(x) for _ in range(3)]
+    rc = load().lb_selftest_log(int(device), _dp(x), x.size, _dp(o[0]), _dp(o[1]), _dp(o[2]))
+    if rc != LB_OK:
+        raise LBError(rc, "lb_selftest_log")
+    return o

@@ -2,6 +2,7 @@
 // argument validation, launches on the context stream and read-back.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -24,6 +25,7 @@ struct lb_ctx {
     int nparts = 0;
     double *diag = nullptr;  // [N + 3]
     unsigned *err = nullptr;
+    LogTables *tbl = nullptr;  // device copy of the log tables
     cudaStream_t stream = nullptr;
     DevParams dp{};
     int64_t steps = 0, launches = 0;
@@ -77,9 +79,12 @@ cudaError_t run_step(lb_ctx *c) {
     a.tile_x = c->p.tile_x;
     a.tile_y = c->p.tile_y;
     a.stream = c->stream;
-    bool mixed = c->p.precision == LB_FP32_MIXED;
-    if (c->p.lattice == LB_D1Q3) return mixed ? d1q3_mixed_step(a) : d1q3_f64_step(a);
-    return mixed ? d2q9_mixed_step(a) : d2q9_f64_step(a);
+    const bool d1 = c->p.lattice == LB_D1Q3;
+    switch (c->p.precision) {
+        case LB_FP32_MIXED: return d1 ? d1q3_tbl_step(a) : d2q9_tbl_step(a);
+        case LB_FP32_DFMU: return d1 ? d1q3_df_step(a) : d2q9_df_step(a);
+        default: return d1 ? d1q3_f64_step(a) : d2q9_f64_step(a);
+    }
 }
 
 FieldLaunch field_args(lb_ctx *c) {
@@ -99,12 +104,12 @@ FieldLaunch field_args(lb_ctx *c) {
 }
 
 cudaError_t run_field(lb_ctx *c, int which, const FieldLaunch &a) {
-    bool mixed = c->p.precision == LB_FP32_MIXED;
+    bool f32 = c->p.precision != LB_FP64;
     bool d1 = c->p.lattice == LB_D1Q3;
     switch (which) {
-        case 0: return d1 ? (mixed ? d1q3_mixed_init(a) : d1q3_f64_init(a)) : (mixed ? d2q9_mixed_init(a) : d2q9_f64_init(a));
-        case 1: return d1 ? (mixed ? d1q3_mixed_moments(a) : d1q3_f64_moments(a)) : (mixed ? d2q9_mixed_moments(a) : d2q9_f64_moments(a));
-        default: return d1 ? (mixed ? d1q3_mixed_diag(a) : d1q3_f64_diag(a)) : (mixed ? d2q9_mixed_diag(a) : d2q9_f64_diag(a));
+        case 0: return d1 ? (f32 ? d1q3_f32_init(a) : d1q3_f64_init(a)) : (f32 ? d2q9_f32_init(a) : d2q9_f64_init(a));
+        case 1: return d1 ? (f32 ? d1q3_f32_moments(a) : d1q3_f64_moments(a)) : (f32 ? d2q9_f32_moments(a) : d2q9_f64_moments(a));
+        default: return d1 ? (f32 ? d1q3_f32_diag(a) : d1q3_f64_diag(a)) : (f32 ? d2q9_f32_diag(a) : d2q9_f64_diag(a));
     }
 }
 
@@ -150,7 +155,46 @@ struct StateHeader {
 };
 static_assert(sizeof(StateHeader) == 64, "state header is 64 bytes");
 
+void split_float(double v, float &hi, float &lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
 }  // namespace
+
+namespace lbvdw {
+
+// Tables of the table-driven logarithms (lb_mu.cuh).  c_j = 1 + j/128; r_j = 1/c_j
+// rounded to the working type; T_j = -ln(r_j) in extended precision, split into
+// hi + lo.  ln 2 comes from its decimal expansion.
+void fill_log_tables(LogTables *t) {
+    const long double ln2 = strtold("0.69314718055994530941723212145817656807550013436", nullptr);
+    for (int j = 0; j < LOG_TBL; ++j) {
+        long double cj = 1.0L + (long double)j / LOG_TBL;
+        double r64 = (double)(1.0L / cj);
+        long double T64 = -logl((long double)r64);
+        t->r64[j] = r64;
+        t->t64_hi[j] = (double)T64;
+        t->t64_lo[j] = (double)(T64 - (long double)t->t64_hi[j]);
+        float r32 = (float)(1.0L / cj);
+        long double T32 = -logl((long double)r32);
+        t->r32[j] = r32;
+        t->t32_hi[j] = (float)T32;
+        t->t32_lo[j] = (float)(T32 - (long double)t->t32_hi[j]);
+    }
+    // FP64 hi: ln 2 with its low 21 significand bits cleared (e * hi exact for |e| < 2^10)
+    double h = (double)ln2;
+    uint64_t bits;
+    std::memcpy(&bits, &h, sizeof bits);
+    bits &= ~((uint64_t(1) << 21) - 1);
+    std::memcpy(&h, &bits, sizeof bits);
+    t->ln2_hi_d = h;
+    t->ln2_lo_d = (double)(ln2 - (long double)h);
+    t->ln2_hi_f = (float)ln2;
+    t->ln2_lo_f = (float)(ln2 - (long double)t->ln2_hi_f);
+}
+
+}  // namespace lbvdw
 
 extern "C" {
 
@@ -176,7 +220,8 @@ lb_status lb_create(const lb_params *p, lb_ctx **out) {
     if (p->abi != LBVDW_ABI) return LB_E_INVALID;
     if (p->lattice != LB_D1Q3 && p->lattice != LB_D2Q9) return LB_E_INVALID;
     if (N < 1 || N > 4) return LB_E_INVALID;
-    if (p->precision != LB_FP64 && p->precision != LB_FP32_MIXED) return LB_E_INVALID;
+    if (p->precision != LB_FP64 && p->precision != LB_FP32_MIXED && p->precision != LB_FP32_DFMU)
+        return LB_E_INVALID;
     if (p->force_method != LB_FORCE_LOG && p->force_method != LB_FORCE_NID) return LB_E_INVALID;
     if (p->nx < 2) return LB_E_INVALID;
     if (p->lattice == LB_D1Q3 ? p->ny != 1 : p->ny < 2) return LB_E_INVALID;
@@ -205,7 +250,7 @@ lb_status lb_create(const lb_params *p, lb_ctx **out) {
     bool tile_ok = p->lattice == LB_D1Q3
                        ? (c->p.tile_y == 1 && (c->p.tile_x == 128 || c->p.tile_x == 256))
                        : ((c->p.tile_x == 32 && c->p.tile_y == 8) || (c->p.tile_x == 64 && c->p.tile_y == 4) ||
-                          (c->p.tile_x == 32 && c->p.tile_y == 16));
+                          (c->p.tile_x == 32 && c->p.tile_y == 16) || (c->p.tile_x == 64 && c->p.tile_y == 8));
     if (!tile_ok) { delete c; return LB_E_INVALID; }
     c->Q = p->lattice == LB_D1Q3 ? 3 : 9;
     c->D = p->lattice == LB_D1Q3 ? 1 : 2;
@@ -224,7 +269,8 @@ lb_status lb_create(const lb_params *p, lb_ctx **out) {
               cudaMalloc(&c->mom, sizeof(double) * N * c->D * c->n) == cudaSuccess &&
               cudaMalloc(&c->partial, sizeof(double) * (N + 3) * nparts) == cudaSuccess &&
               cudaMalloc(&c->diag, sizeof(double) * (N + 3)) == cudaSuccess &&
-              cudaMalloc(&c->err, sizeof(unsigned)) == cudaSuccess;
+              cudaMalloc(&c->err, sizeof(unsigned)) == cudaSuccess &&
+              cudaMalloc(&c->tbl, sizeof(LogTables)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         lb_destroy(c);
@@ -248,6 +294,18 @@ lb_status lb_create(const lb_params *p, lb_ctx **out) {
         d.rho_ref[k] = 0.0;
     }
     d.err = c->err;
+    d.tbl = c->tbl;
+    d.gkT = p->gamma_mu * p->kT;
+    for (int k = 0; k < 4; ++k) split_float(p->b[k], d.b_hi[k], d.b_lo[k]);
+    split_float(d.gkT, d.gkT_hi, d.gkT_lo);
+    split_float(p->gamma_mu, d.gamma_hi, d.gamma_lo);
+    LogTables h;
+    fill_log_tables(&h);
+    if (cudaMemcpy(c->tbl, &h, sizeof h, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        lb_destroy(c);
+        return LB_E_CUDA;
+    }
     *out = c;
     return LB_OK;
 }
@@ -255,8 +313,11 @@ lb_status lb_create(const lb_params *p, lb_ctx **out) {
 static lb_status init_common(lb_ctx *c, const double *rho_dev, const double *mom_dev, const double *rho_ref) {
     const int N = c->p.ncomp;
     for (int k = 0; k < 4; ++k) c->dp.rho_ref[k] = 0.0;
-    if (c->p.precision == LB_FP32_MIXED)
-        for (int k = 0; k < N; ++k) c->dp.rho_ref[k] = c->p.rho_ref[k] > 0.0 ? c->p.rho_ref[k] : rho_ref[k];
+    // FP32 storage: the reference density is rounded to a float value, so the float
+    // kernels and the FP64 moment sums use the same number
+    if (c->p.precision != LB_FP64)
+        for (int k = 0; k < N; ++k)
+            c->dp.rho_ref[k] = (double)(float)(c->p.rho_ref[k] > 0.0 ? c->p.rho_ref[k] : rho_ref[k]);
     LB_CUDA(c, cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
     c->cur = 0;
     FieldLaunch a = field_args(c);
@@ -310,7 +371,7 @@ lb_status lb_init_fields_dev(lb_ctx *c, const double *rho_dev, const double *mom
     LB_CUDA(c, cudaSetDevice(c->p.device));
     double mean[4] = {0, 0, 0, 0};
     bool need_mean = false;
-    if (c->p.precision == LB_FP32_MIXED)
+    if (c->p.precision != LB_FP64)
         for (int k = 0; k < N; ++k) need_mean = need_mean || !(c->p.rho_ref[k] > 0.0);
     if (need_mean) {
         // mean densities through the diagnostics reduction (one synchronisation)
@@ -433,7 +494,7 @@ lb_status lb_load_state(lb_ctx *c, const void *buf, size_t bytes) {
         h.hash != params_hash(c->p))
         return fail(c, LB_E_INVALID, "saved state does not match this context");
     LB_CUDA(c, cudaSetDevice(c->p.device));
-    if (c->p.precision == LB_FP32_MIXED) {
+    if (c->p.precision != LB_FP64) {
         double sum = 0.0;
         for (int k = 0; k < 4; ++k) sum += c->dp.rho_ref[k] * (k + 1);
         if (!c->has_state || sum != h.rho_ref_sum)
@@ -467,6 +528,7 @@ lb_status lb_destroy(lb_ctx *c) {
     cudaFree(c->partial);
     cudaFree(c->diag);
     cudaFree(c->err);
+    cudaFree(c->tbl);
     delete c;
     return LB_OK;
 }

@@ -1,0 +1,8 @@
+// D1Q3 lattice, FP32 deviation storage; FP64 eta, 1/eta and table-driven logs in mu.
+#define LBVDW_LAT 1
+#define LBVDW_S float
+#define LBVDW_R float
+#define LBVDW_MU MU_TBL
+#define LBVDW_NAME d1q3_tbl
+#define LBVDW_FIELDS d1q3_f32
+#include "lb_tu.cuh"

@@ -3,7 +3,7 @@
 //
 // One CTA owns a TX x TY tile of nodes.  A timestep is one launch:
 //   phase 1  densities rho^c on the tile plus a 2-node ring        (Sec. III moments)
-//   phase 2  mu^c on the tile plus a 1-node ring, FP64            (Eq. discreteChemicalPotential)
+//   phase 2  mu^c on the tile plus a 1-node ring                   (Eq. discreteChemicalPotential)
 //   phase 3  per node: force (Eq. forceMuLog / forceMuId), friction (Eq. forceFriction),
 //            Psi (Eq. forceCorrectionsPsi), BGK + forcing (Eqs. feq, BGKcollisionOperator),
 //            push-streaming to the other buffer (Eq. LBequation).
@@ -12,10 +12,13 @@
 //
 // Storage type S holds the deviation g_i^c = f_i^c - w_i rho_ref^c (rho_ref = 0 in the
 // FP64 path, so g = f there).  Compute type R is double in the FP64 path and float in
-// the mixed path; mu^c, eta, 1/eta and the logs are always double.
+// the mixed paths, where eta, 1/eta, the logarithms and the differences of mu are
+// carried in FP64 (MU_TBL) or in double-float arithmetic (MU_DF), see lb_mu.cuh.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+
+#include "lb_mu.cuh"
 
 namespace lbvdw {
 
@@ -29,8 +32,12 @@ struct DevParams {
     double kT, gamma;
     double a[16], kappa[16], lam[16];  // stride 4
     double b[4];
-    double rho_ref[4];
-    unsigned *err;     // error word (device)
+    double rho_ref[4];  // FP32-mixed: reference densities (rounded to float values)
+    unsigned *err;      // error word (device)
+    const LogTables *tbl;  // log tables (device)
+    double gkT;         // gamma_mu * kT
+    float b_hi[4], b_lo[4];  // double-float copies of b, gamma kT and gamma
+    float gkT_hi, gkT_lo, gamma_hi, gamma_lo;
 };
 
 // ---------------------------------------------------------------------------
@@ -97,113 +104,263 @@ __device__ __forceinline__ T lap_at(const T *s, int ex, int ey, int EXW) {
 
 // ---------------------------------------------------------------------------
 // the fused step
+//
+// MU selects the chemical-potential arithmetic:
+//   MU_F64   FP64 path: everything in double, CUDA's log and division;
+//   MU_TBL   mixed path: FP64 eta, 1/eta and table-driven FP64 logs (lb_mu.cuh),
+//            FP32 for the linear part of mu, the stencils and everything after;
+//   MU_DF    mixed path with the FP64 work replaced by double-float arithmetic.
+// The differences of mu across a node (the only place where mu's extra precision
+// matters) are taken in the mu arithmetic, then rounded to R.
 // ---------------------------------------------------------------------------
-template <int LAT, int N, int TX, int TY, class S, class R, int FORCE>
+enum { MU_F64 = 0, MU_TBL = 1, MU_DF = 2 };
+
+template <int MU> struct MuStore;
+template <> struct MuStore<MU_F64> { using T = double; };
+template <> struct MuStore<MU_TBL> { using T = double; };
+template <> struct MuStore<MU_DF> { using T = df; };
+
+// phi difference a - b in the mu arithmetic, rounded to R
+template <class R>
+__device__ __forceinline__ R phi_diff(double a, double b) { return (R)(a - b); }
+template <class R>
+__device__ __forceinline__ R phi_diff(df a, df b) { return (R)df_to_float(df_add(a, df_neg(b))); }
+
+// D phi at (mx, my) of an MX-wide shared array, differences in the mu arithmetic
+template <int LAT, class R, class T>
+__device__ __forceinline__ void grad_phi(const T *s, int mx, int my, int MXW, R &gx, R &gy) {
+    const T *p = s + my * MXW + mx;
+    if constexpr (LAT == 1) {
+        gx = (R)0.5 * phi_diff<R>(p[1], p[-1]);
+        gy = (R)0;
+    } else {
+        R ew = phi_diff<R>(p[1], p[-1]);
+        R ns = phi_diff<R>(p[MXW], p[-MXW]);
+        R d1 = phi_diff<R>(p[MXW + 1], p[-MXW - 1]);  // NE - SW
+        R d2 = phi_diff<R>(p[-MXW + 1], p[MXW - 1]);  // SE - NW
+        gx = ew * (R)(1.0 / 3.0) + (d1 + d2) * (R)(1.0 / 12.0);
+        gy = ns * (R)(1.0 / 3.0) + (d1 - d2) * (R)(1.0 / 12.0);
+    }
+}
+
+template <int LAT, int N, int TX, int TY, class S, class R, int FORCE, int MU>
 __global__ void __launch_bounds__(TX *TY)
     lb_step_kernel(const S *__restrict__ fin, S *__restrict__ fout, DevParams P) {
     using L = Lat<LAT>;
+    using MT = typename MuStore<MU>::T;
     constexpr int Q = L::Q;
     constexpr int HY = L::HY;
     constexpr int EX = TX + 4, EY = TY + 4 * HY;  // densities: tile + 2 ring
     constexpr int MX = TX + 2, MY = TY + 2 * HY;  // mu: tile + 1 ring
     constexpr int NT = TX * TY;
+    constexpr int RING = EX * EY - TX * TY;
+    // keep the node's own populations in registers when they fit comfortably
+    constexpr bool KEEP = sizeof(S) * N * Q <= 144;
+    static_assert(MU == MU_F64 ? sizeof(R) == 8 : sizeof(R) == 4, "MU and R mismatch");
 
-    __shared__ double s_rho[N][EY * EX];
-    __shared__ double s_phi[N][MY * MX];  // gamma mu (log) or gamma mu - theta ln rho (nid)
+    __shared__ R s_rho[N][EY * EX];
+    __shared__ MT s_phi[N][MY * MX];  // gamma mu (log) or gamma mu - theta ln rho (nid)
+    constexpr int TBL_WORDS = MU == MU_TBL ? 3 * LOG_TBL * 2 : (MU == MU_DF ? 3 * LOG_TBL : 1);
+    __shared__ __align__(16) float s_tbl[TBL_WORDS];
 
     const int nx = P.nx, ny = P.ny;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int tid = threadIdx.x + TX * threadIdx.y;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = tx + TX * ty;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool inside = x < nx && y < ny;
 
-    // ---- phase 1: rho^c on tile + 2 ring ------------------------------------
-    for (int k = tid; k < EX * EY; k += NT) {
-        int ex = k % EX, ey = k / EX;
-        int gx = wrap(x0 + ex - 2, nx);
-        int gy = (LAT == 1) ? 0 : wrap(y0 + ey - 2, ny);
+    if constexpr (MU == MU_TBL) {
+        double *t = reinterpret_cast<double *>(s_tbl);
+        for (int k = tid; k < LOG_TBL; k += NT) {
+            t[k] = P.tbl->r64[k];
+            t[LOG_TBL + k] = P.tbl->t64_hi[k];
+            t[2 * LOG_TBL + k] = P.tbl->t64_lo[k];
+        }
+    } else if constexpr (MU == MU_DF) {
+        for (int k = tid; k < LOG_TBL; k += NT) {
+            s_tbl[k] = P.tbl->r32[k];
+            s_tbl[LOG_TBL + k] = P.tbl->t32_hi[k];
+            s_tbl[2 * LOG_TBL + k] = P.tbl->t32_lo[k];
+        }
+    }
+
+    // ---- phase 1a: own node -> registers, rho^c -> shared -------------------
+    S g[KEEP ? N : 1][KEEP ? Q : 1];
+    R jx[N], jy[N];
+    {
+        const int gx = inside ? x : wrap(x, nx), gy = inside ? y : (LAT == 1 ? 0 : wrap(y, ny));
+        const int ex = tx + 2, ey = ty + 2 * HY;
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            R acc = (R)0, ax = (R)0, ay = (R)0;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                S v = fin[pop_index(c, i, Q, gy, gx, nx, ny)];
+                if constexpr (KEEP) g[c][i] = v;
+                R rv = (R)v;
+                acc += rv;
+                if (L::vx(i) == 1) ax += rv;
+                if (L::vx(i) == -1) ax -= rv;
+                if (L::vy(i) == 1) ay += rv;
+                if (L::vy(i) == -1) ay -= rv;
+            }
+            s_rho[c][ey * EX + ex] = (R)P.rho_ref[c] + acc;
+            jx[c] = ax;
+            jy[c] = ay;
+        }
+    }
+    // ---- phase 1b: rho^c on the 2-node ring -----------------------------------
+    for (int k = tid; k < RING; k += NT) {
+        int ex, ey;
+        if constexpr (LAT == 1) {
+            ey = 0;
+            ex = k < 2 ? k : EX - 4 + k;
+        } else {
+            if (k < 2 * EX) {
+                ey = k / EX;
+                ex = k - ey * EX;
+            } else if (k < 4 * EX) {
+                int kk = k - 2 * EX;
+                ey = EY - 2 + kk / EX;
+                ex = kk % EX;
+            } else {
+                int kk = k - 4 * EX;
+                ey = 2 + (kk >> 2);
+                int col = kk & 3;
+                ex = col < 2 ? col : EX - 4 + col;
+            }
+        }
+        const int gx = wrap(x0 + ex - 2, nx);
+        const int gy = (LAT == 1) ? 0 : wrap(y0 + ey - 2, ny);
 #pragma unroll
         for (int c = 0; c < N; ++c) {
             R acc = (R)0;
 #pragma unroll
             for (int i = 0; i < Q; ++i) acc += (R)fin[pop_index(c, i, Q, gy, gx, nx, ny)];
-            s_rho[c][k] = P.rho_ref[c] + (double)acc;
+            s_rho[c][ey * EX + ex] = (R)P.rho_ref[c] + acc;
         }
     }
     __syncthreads();
 
-    // ---- phase 2: mu^c (FP64) on tile + 1 ring --------------------------------
+    // ---- phase 2: phi^c = gamma mu^c (- theta ln rho^c for "nid") on tile + 1 --
     unsigned bad = 0;
     for (int k = tid; k < MX * MY; k += NT) {
-        int mx = k % MX, my = k / MX;
-        int ex = mx + 1, ey = my + HY;
-        double r[N], lp[N];
-        double eta = 1.0, rt = 0.0;
+        const int mx = k % MX, my = k / MX;
+        const int ex = mx + 1, ey = my + HY;
+        R r[N], lin[N];
+        bool ok = true;
 #pragma unroll
         for (int c = 0; c < N; ++c) {
             r[c] = s_rho[c][ey * EX + ex];
-            lp[c] = lap_at<LAT, double>(s_rho[c], ex, ey, EX);
-            eta -= P.b[c] * r[c];
-            rt += r[c];
+            ok = ok && (r[c] > (R)0);
         }
-        bool ok = eta > 0.0;
+        // linear part sum_c' (2 a rho' + kappa Lap rho'), in R
 #pragma unroll
-        for (int c = 0; c < N; ++c) ok = ok && (r[c] > 0.0);
+        for (int c = 0; c < N; ++c) lin[c] = (R)0;
+#pragma unroll
+        for (int cc = 0; cc < N; ++cc) {
+            R lp = lap_at<LAT, R>(s_rho[cc], ex, ey, EX);
+#pragma unroll
+            for (int c = 0; c < N; ++c) lin[c] += (R)(2.0 * P.a[c * 4 + cc]) * r[cc] + (R)P.kappa[c * 4 + cc] * lp;
+        }
+        if constexpr (MU == MU_F64) {
+            double eta = 1.0, rt = 0.0;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                eta -= P.b[c] * r[c];
+                rt += r[c];
+            }
+            ok = ok && eta > 0.0;
+            const double ieta = 1.0 / eta;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                double m = P.kT * (log(r[c] * ieta) + P.b[c] * rt * ieta) - lin[c];
+                double ph = P.gamma * m;
+                if constexpr (FORCE == 1) ph -= (1.0 / 3.0) * log(r[c]);
+                s_phi[c][k] = ph;
+            }
+        } else if constexpr (MU == MU_TBL) {
+            const double *t = reinterpret_cast<const double *>(s_tbl);
+            double eta = 1.0, rt = 0.0;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                eta = fma(-P.b[c], (double)r[c], eta);
+                rt += (double)r[c];
+            }
+            ok = ok && eta > 0.0;
+            double y = (double)__frcp_rn((float)eta);  // Newton: y <- y + y (1 - eta y), twice
+            y = fma(y, fma(-eta, y, 1.0), y);
+            y = fma(y, fma(-eta, y, 1.0), y);
+            const double rte = rt * y;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                double lg = ok ? log64_tbl((double)r[c] * y, t, t + LOG_TBL, t + 2 * LOG_TBL, P.tbl->ln2_hi_d,
+                                           P.tbl->ln2_lo_d)
+                               : 0.0;
+                double ph = fma(P.gkT, fma(P.b[c], rte, lg), -P.gamma * (double)lin[c]);
+                if constexpr (FORCE == 1)
+                    ph -= (1.0 / 3.0) * (ok ? log64_tbl((double)r[c], t, t + LOG_TBL, t + 2 * LOG_TBL,
+                                                         P.tbl->ln2_hi_d, P.tbl->ln2_lo_d)
+                                            : 0.0);
+                s_phi[c][k] = ph;
+            }
+        } else {  // MU_DF
+            df eta = {1.0f, 0.0f}, rt = {0.0f, 0.0f};
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                eta = df_add(eta, df_neg(df_mul_f({P.b_hi[c], P.b_lo[c]}, r[c])));
+                rt = df_add(rt, {r[c], 0.0f});
+            }
+            ok = ok && eta.hi > 0.0f;
+            const df ieta = df_recip(eta);
+            const df rte = df_mul(rt, ieta);
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                df lg = ok ? df_log(df_mul_f(ieta, r[c]), s_tbl, s_tbl + LOG_TBL, s_tbl + 2 * LOG_TBL,
+                                    P.tbl->ln2_hi_f, P.tbl->ln2_lo_f)
+                           : df{0.0f, 0.0f};
+                df m = df_add(lg, df_mul(rte, {P.b_hi[c], P.b_lo[c]}));
+                df ph = df_add(df_mul(m, {P.gkT_hi, P.gkT_lo}), df_neg(df_mul_f({P.gamma_hi, P.gamma_lo}, lin[c])));
+                if constexpr (FORCE == 1) {
+                    df lr = ok ? df_log({r[c], 0.0f}, s_tbl, s_tbl + LOG_TBL, s_tbl + 2 * LOG_TBL, P.tbl->ln2_hi_f,
+                                        P.tbl->ln2_lo_f)
+                               : df{0.0f, 0.0f};
+                    ph = df_add(ph, df_neg(df_mul_f(lr, 1.0f / 3.0f)));
+                }
+                s_phi[c][k] = ph;
+            }
+        }
         if (!ok) bad = 1;
-        double ieta = 1.0 / eta;
-#pragma unroll
-        for (int c = 0; c < N; ++c) {
-            double m = P.kT * (log(r[c] * ieta) + P.b[c] * rt * ieta);
-#pragma unroll
-            for (int cc = 0; cc < N; ++cc) m -= 2.0 * P.a[c * 4 + cc] * r[cc] + P.kappa[c * 4 + cc] * lp[cc];
-            double ph = P.gamma * m;
-            if constexpr (FORCE == 1) ph -= (1.0 / 3.0) * log(r[c]);
-            s_phi[c][k] = ph;
-        }
     }
     __syncthreads();
+    if (bad) atomicOr(P.err, ERR_DOMAIN);
+    if (!inside) return;
 
     // ---- phase 3: forces, collision, streaming --------------------------------
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x = x0 + tx, y = y0 + ty;
-    if (x >= nx || y >= ny) {
-        if (bad) atomicOr(P.err, ERR_DOMAIN);
-        return;
-    }
     const int ex = tx + 2, ey = ty + 2 * HY;
     const int mx = tx + 1, my = ty + HY;
 
     R rho[N], ux[N], uy[N], Gx[N], Gy[N], lap[N];
 #pragma unroll
     for (int c = 0; c < N; ++c) {
-        double rd = s_rho[c][ey * EX + ex];
-        rho[c] = (R)rd;
-        lap[c] = (R)lap_at<LAT, double>(s_rho[c], ex, ey, EX);
-        double gpx, gpy;
-        grad_at<LAT, double>(s_phi[c], mx, my, MX, gpx, gpy);
-        double gmx, gmy;
+        const R rd = s_rho[c][ey * EX + ex];
+        rho[c] = rd;
+        lap[c] = lap_at<LAT, R>(s_rho[c], ex, ey, EX);
+        R gpx, gpy;
+        grad_phi<LAT, R, MT>(s_phi[c], mx, my, MX, gpx, gpy);
         if constexpr (FORCE == 0) {
-            double grx, gry;
-            grad_at<LAT, double>(s_rho[c], ex, ey, EX, grx, gry);
-            gmx = -rd * gpx + (1.0 / 3.0) * grx;
-            gmy = -rd * gpy + (1.0 / 3.0) * gry;
+            R grx, gry;
+            grad_at<LAT, R>(s_rho[c], ex, ey, EX, grx, gry);
+            Gx[c] = -rd * gpx + (R)(1.0 / 3.0) * grx;
+            Gy[c] = -rd * gpy + (R)(1.0 / 3.0) * gry;
         } else {
-            gmx = -rd * gpx;
-            gmy = -rd * gpy;
+            Gx[c] = -rd * gpx;
+            Gy[c] = -rd * gpy;
         }
-        Gx[c] = (R)gmx;
-        Gy[c] = (R)gmy;
-        // bare momentum of this node
-        R jx = (R)0, jy = (R)0;
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            R g = (R)fin[pop_index(c, i, Q, y, x, nx, ny)];
-            if (L::vx(i) == 1) jx += g;
-            if (L::vx(i) == -1) jx -= g;
-            if (L::vy(i) == 1) jy += g;
-            if (L::vy(i) == -1) jy -= g;
-        }
-        R ir = (R)1 / rho[c];
-        ux[c] = jx * ir;
-        uy[c] = jy * ir;
+        const R ir = (R)1 / rd;
+        ux[c] = jx[c] * ir;
+        uy[c] = jy[c] * ir;
     }
 
     // friction with the implicit u-hat: (D + L/2) h = -L u0, G^f = D h  (per direction)
@@ -249,10 +406,10 @@ __global__ void __launch_bounds__(TX *TY)
             }
 #pragma unroll
             for (int k = N - 1; k >= 0; --k) {
-                R s = h[k];
+                R sacc = h[k];
 #pragma unroll
-                for (int c2 = k + 1; c2 < N; ++c2) s -= M[k][c2] * h[c2];
-                h[k] = s / M[k][k];
+                for (int c2 = k + 1; c2 < N; ++c2) sacc -= M[k][c2] * h[c2];
+                h[k] = sacc / M[k][k];
             }
 #pragma unroll
             for (int c = 0; c < N; ++c) {
@@ -272,7 +429,7 @@ __global__ void __launch_bounds__(TX *TY)
         const R Syy = (R)2 * gy * v + cg * gy * gy * ir + cl * lap[c];
         const R Sxy = gx * v + u * gy + cg * gx * gy * ir;
         const R usq = u * u + v * v;
-        const R drho = (R)((double)s_rho[c][ey * EX + ex] - P.rho_ref[c]);
+        const R drho = r - (R)P.rho_ref[c];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             constexpr R third = (R)(1.0 / 3.0);
@@ -285,14 +442,15 @@ __global__ void __launch_bounds__(TX *TY)
             R SQ = Sxx * ((R)(cx * cx) - third);
             if constexpr (LAT == 2) SQ += Syy * ((R)(cy * cy) - third) + (R)2 * Sxy * (R)(cx * cy);
             const R Fi = wi * ((R)3 * vG + (R)4.5 * SQ);
-            const R g = (R)fin[pop_index(c, i, Q, y, x, nx, ny)];
-            const R post = g + omega * (feq_dev - g) + Fi;
-            const int dx = (LAT == 1) ? wrap(x + cx, nx) : wrap(x + cx, nx);
+            R gi;
+            if constexpr (KEEP) gi = (R)g[c][i];
+            else gi = (R)fin[pop_index(c, i, Q, y, x, nx, ny)];
+            const R post = gi + omega * (feq_dev - gi) + Fi;
+            const int dx = wrap(x + cx, nx);
             const int dy = (LAT == 1) ? 0 : wrap(y + cy, ny);
             fout[pop_index(c, i, Q, dy, dx, nx, ny)] = (S)post;
         }
     }
-    if (bad) atomicOr(P.err, ERR_DOMAIN);
 }
 
 // ---------------------------------------------------------------------------

@@ -28,18 +28,23 @@ struct FieldLaunch {
     cudaStream_t stream;
 };
 
-// supported step tiles (tile_x, tile_y) per lattice; returns false when not compiled
-bool step_tile_supported(int lattice, int tile_x, int tile_y);
+// step launchers: one per lattice and chemical-potential arithmetic
+cudaError_t d1q3_f64_step(const StepLaunch &a);
+cudaError_t d1q3_tbl_step(const StepLaunch &a);
+cudaError_t d1q3_df_step(const StepLaunch &a);
+cudaError_t d2q9_f64_step(const StepLaunch &a);
+cudaError_t d2q9_tbl_step(const StepLaunch &a);
+cudaError_t d2q9_df_step(const StepLaunch &a);
 
-#define LBVDW_DECLARE(NAME)                                \
-    cudaError_t NAME##_step(const StepLaunch &a);          \
+// field launchers: one per lattice and storage type (double / float)
+#define LBVDW_DECLARE_FIELDS(NAME)                         \
     cudaError_t NAME##_init(const FieldLaunch &a);         \
     cudaError_t NAME##_moments(const FieldLaunch &a);      \
     cudaError_t NAME##_diag(const FieldLaunch &a);
-LBVDW_DECLARE(d1q3_f64)
-LBVDW_DECLARE(d1q3_mixed)
-LBVDW_DECLARE(d2q9_f64)
-LBVDW_DECLARE(d2q9_mixed)
-#undef LBVDW_DECLARE
+LBVDW_DECLARE_FIELDS(d1q3_f64)
+LBVDW_DECLARE_FIELDS(d1q3_f32)
+LBVDW_DECLARE_FIELDS(d2q9_f64)
+LBVDW_DECLARE_FIELDS(d2q9_f32)
+#undef LBVDW_DECLARE_FIELDS
 
 }  // namespace lbvdw

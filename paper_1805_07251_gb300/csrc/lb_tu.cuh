@@ -1,6 +1,8 @@
 // lb_tu.cuh -- body of one lattice/precision translation unit.  Before including,
 // define LBVDW_LAT (1 = D1Q3, 2 = D2Q9), LBVDW_S / LBVDW_R (storage and compute
-// types) and LBVDW_NAME (prefix of the launch functions).
+// types), LBVDW_MU (chemical-potential arithmetic, MU_*), LBVDW_NAME (prefix of the
+// step launcher) and, in one unit per storage type, LBVDW_FIELDS (prefix of the
+// init / moments / diagnostics launchers).
 #include "lb_launch.cuh"
 
 namespace lbvdw {
@@ -10,12 +12,13 @@ namespace {
 constexpr int LATV = LBVDW_LAT;
 using SV = LBVDW_S;
 using RV = LBVDW_R;
+constexpr int MUV = LBVDW_MU;
 
 template <int N, int TX, int TY, int FORCE>
 cudaError_t step_one(const StepLaunch &a) {
     dim3 block(TX, TY);
     dim3 grid((a.P.nx + TX - 1) / TX, LATV == 1 ? 1 : (a.P.ny + TY - 1) / TY);
-    lb_step_kernel<LATV, N, TX, TY, SV, RV, FORCE><<<grid, block, 0, a.stream>>>(
+    lb_step_kernel<LATV, N, TX, TY, SV, RV, FORCE, MUV><<<grid, block, 0, a.stream>>>(
         static_cast<const SV *>(a.fin), static_cast<SV *>(a.fout), a.P);
     return cudaGetLastError();
 }
@@ -81,11 +84,14 @@ cudaError_t LBVDW_CAT(LBVDW_NAME, _step)(const StepLaunch &a) {
     if (a.tile_x == 32 && a.tile_y == 8) return step_f<32, 8>(a);
     if (a.tile_x == 64 && a.tile_y == 4) return step_f<64, 4>(a);
     if (a.tile_x == 32 && a.tile_y == 16) return step_f<32, 16>(a);
+    if (a.tile_x == 64 && a.tile_y == 8) return step_f<64, 8>(a);
     return cudaErrorInvalidConfiguration;
 #endif
 }
 
-cudaError_t LBVDW_CAT(LBVDW_NAME, _init)(const FieldLaunch &a) {
+#ifdef LBVDW_FIELDS
+
+cudaError_t LBVDW_CAT(LBVDW_FIELDS, _init)(const FieldLaunch &a) {
     switch (a.ncomp) {
         case 1: return init_one<1>(a);
         case 2: return init_one<2>(a);
@@ -95,7 +101,7 @@ cudaError_t LBVDW_CAT(LBVDW_NAME, _init)(const FieldLaunch &a) {
     return cudaErrorInvalidValue;
 }
 
-cudaError_t LBVDW_CAT(LBVDW_NAME, _moments)(const FieldLaunch &a) {
+cudaError_t LBVDW_CAT(LBVDW_FIELDS, _moments)(const FieldLaunch &a) {
     switch (a.ncomp) {
         case 1: return moments_one<1>(a);
         case 2: return moments_one<2>(a);
@@ -105,7 +111,7 @@ cudaError_t LBVDW_CAT(LBVDW_NAME, _moments)(const FieldLaunch &a) {
     return cudaErrorInvalidValue;
 }
 
-cudaError_t LBVDW_CAT(LBVDW_NAME, _diag)(const FieldLaunch &a) {
+cudaError_t LBVDW_CAT(LBVDW_FIELDS, _diag)(const FieldLaunch &a) {
     switch (a.ncomp) {
         case 1: return diag_one<1>(a);
         case 2: return diag_one<2>(a);
@@ -114,5 +120,6 @@ cudaError_t LBVDW_CAT(LBVDW_NAME, _diag)(const FieldLaunch &a) {
     }
     return cudaErrorInvalidValue;
 }
+#endif  // LBVDW_FIELDS
 
 }  // namespace lbvdw
