@@ -154,6 +154,29 @@ lb_status lb_read_moments_dev(lb_ctx *ctx, double *rho_dev, double *mom_dev);
  * Synchronises; reports flagged errors. */
 lb_status lb_free_energy(lb_ctx *ctx, double *F, double *mass, double *mom_total);
 
+/* No-allocation variant of lb_free_energy for callers that cannot allocate device
+ * memory (code inside another framework's memory pool or under a fixed memory budget,
+ * tools handed a bare device pointer to a state, callers that must not trigger an
+ * allocation in the middle of their own stream work).  The paper has no counterpart:
+ * this is an interface convenience, not part of the method.
+ *   p      parameters of the state (lattice, nx, ny, ncomp, precision, kT, a, kappa, b,
+ *          device, stream; rho_ref must be set (> 0) for the FP32 precisions, as the
+ *          stored populations are deviations from w_i rho_ref^c)
+ *   f_dev  device populations [c][i][y][x] in the storage type of p->precision
+ *   out_dev device output of ncomp + 4 doubles: mass[ncomp], F, sum j_x, sum j_y and an
+ *          error flag (1.0 when a density or eta <= 0 or a non-finite value was met)
+ * Enqueued on p->stream; returns without synchronising.  All scratch lives in one static
+ * device array of 2^21 doubles (16 MiB) that every GPU loading the library holds until
+ * exit; it fits ncomp * (1 + d) * nx * ny <= 2^21 - 7169 doubles (d = 1 for D1Q3, 2 for
+ * D2Q9), e.g. a 512 x 512 D2Q9 lattice with two components; larger states are rejected
+ * with LB_E_INVALID.  Every call shares the array and it keeps the last call's contents
+ * (the error word is cleared at the start of each call); calls that overlap on the GPU
+ * race, so serialise them.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current: make it before any stream
+ * capture.  Calls no cudaMalloc, cudaFree or allocating library routine.
+ * Errors: LB_E_INVALID, LB_E_CUDA. */
+lb_status lb_free_energy_noalloc(const lb_params *p, const void *f_dev, double *out_dev);
+
 /* Size in bytes of a saved state, and save/load of the raw populations
  * ([c][i][y][x] in the storage type of the precision, plus a 64-byte header with the
  * step counter and a parameter hash).  lb_save_state synchronises; lb_load_state

@@ -87,6 +87,7 @@ def load():
         "lb_status_str": (ctypes.c_char_p, [ctypes.c_int]),
         "lb_last_error": (ctypes.c_char_p, [C]),
         "lb_selftest_log": (ctypes.c_int, [ctypes.c_int32, _DP, ctypes.c_int64, _DP, _DP, _DP]),
+        "lb_free_energy_noalloc": (ctypes.c_int, [P, C, C]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -199,3 +200,10 @@ def lb_selftest_log(device, x):
     if rc != LB_OK:
         raise LBError(rc, "lb_selftest_log")
     return o
+
+
+def lb_free_energy_noalloc(p, f_ptr, out_ptr):
+    """Enqueue the no-allocation diagnostics on p.stream (device pointers in and out)."""
+    rc = load().lb_free_energy_noalloc(ctypes.byref(p), ctypes.c_void_p(f_ptr), ctypes.c_void_p(out_ptr))
+    if rc != LB_OK:
+        raise LBError(rc, "lb_free_energy_noalloc")
