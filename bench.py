@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--tile", default=None, help="D2Q9 tile as TXxTY (default: the library's)")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the batched-sweep measurement")
     ap.add_argument("--only", choices=["fp32_dfmu", "fp32_mixed", "fp64"], default=None,
                     help="time one path only (profiling runs): no e2e, no cpu baseline")
     return ap.parse_args()
@@ -171,11 +173,50 @@ def run_reference(args):
     return 0
 
 
+def time_sweep(torch, dev, precision, steps, warmup, dist):
+    """Batched sweep (workload c3): 256 D1Q3 + 128 D2Q9 independent runs advanced together
+    by CUDA-graph replays; D2Q9 tile from the autotuner.  The state (1.8 GB per step)
+    exceeds the L2, so no flush is needed between steps."""
+    import lbinputs
+    from paper_1805_07251_gb300.batch import Batch, autotune
+
+    recs = lbinputs.sweep_runs()
+    p = lbinputs.base_params("c1")
+    fields = [lbinputs.sweep_fields(r) for r in recs]
+    b = Batch(recs, p["a"], p["b"], p["kappa"], p["lam"], 2, precision=precision, device=dev,
+              stream=torch.cuda.current_stream(dev).cuda_stream)
+    b.init(fields)
+    tile, _ = autotune(b, fields, precision, steps=16)
+    b.step(warmup)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    l0 = b.launches
+    ms = b.time_steps(steps)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    launches = b.launches - l0
+    unstable = int((b.errors() != 0).sum())
+    cn = b.total_component_nodes()
+    world = dist.get_world_size() if dist is not None else 1
+    out = {"value": world * cn * steps / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms / steps,
+           "runs": len(recs), "d1q3_runs": sum(r["lattice"] == "D1Q3" for r in recs),
+           "d2q9_runs": sum(r["lattice"] == "D2Q9" for r in recs), "component_nodes": cn,
+           "tile": "x".join(map(str, tile)) if tile else None, "unstable_runs_after_warmup_and_timed": unstable,
+           "dtype": DTYPES[precision], "gpu_launches": launches,
+           "note": "one CUDA-graph replay per 32 timesteps: D1Q3 runs resident in shared memory, "
+                   "D2Q9 runs as one tile-list launch per timestep"}
+    b.close()
+    return out
+
+
 def time_path(torch, Simulation, kw, rho, precision, steps, warmup, flush, dev):
     """Device time of the fused step kernel: CUDA events on the launching stream around
     each step, L2 flushed before each step outside the events."""
     stream = torch.cuda.current_stream(dev)
-    sim = Simulation(precision=precision, device=dev, stream=stream.cuda_stream, **kw)
+    sim = Simulation(precision=precision, device=dev, stream=stream.cuda_stream, tile=TILE, **kw)
     sim.init(rho)
     for _ in range(warmup):
         flush.zero_()
@@ -186,8 +227,14 @@ def time_path(torch, Simulation, kw, rho, precision, steps, warmup, flush, dev):
     return sim, ev, launches0, stream
 
 
+TILE = None
+
+
 def main():
+    global TILE
     args = parse()
+    if args.tile:
+        TILE = tuple(int(v) for v in args.tile.lower().split("x"))
     if args.impl == "reference":
         return run_reference(args)
     if args.warmup < 3:
@@ -262,6 +309,9 @@ def main():
         results[precision] = dict(value=value, ms=ms, launches=launches, alg_bytes=alg_bytes, achieved=achieved)
         sim.close()
 
+    sweep = None
+    if not args.only and not args.no_sweep:
+        sweep = time_sweep(torch, dev, HEAD, args.steps, args.warmup, dist)
     e2e = None
     if not args.only:
         # end to end through the C ABI with host buffers: pinned host densities in,
@@ -305,7 +355,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPES[HEAD], "data": "synthetic",
         "config": {"workload": "D2Q9, 2 components, 1024x1024 periodic, spinodal mixture (c2), " + HEAD,
-                   "nodes": nodes, "ncomp": N, "tile": "32x8", "l2": "flushed between steps (256 MB write)",
+                   "nodes": nodes, "ncomp": N, "tile": args.tile or "32x8", "l2": "flushed between steps (256 MB write)",
                    "parallelism": "independent replica per GPU" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": head["achieved"], "peak": peak_gbs, "unit": "GB/s",
                      "frac": head["achieved"] / peak_gbs, "traffic": None, "peak_kind": peak_kind,
@@ -315,6 +365,11 @@ def main():
     }
     if e2e is not None:
         line["e2e"] = e2e
+    if sweep is not None:
+        if "fp64" in results:
+            sweep["vs_fp64_single_run"] = sweep["value"] / results["fp64"]["value"]
+        line["batched_sweep"] = sweep
+        line["gpu_launches"] += sweep["gpu_launches"]
     for key, name in (("fp32_mixed", "fp32_fp64mu"), ("fp64", "fp64")):
         if key not in results or key == HEAD:
             continue

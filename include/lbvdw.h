@@ -177,6 +177,78 @@ lb_status lb_free_energy(lb_ctx *ctx, double *F, double *mass, double *mom_total
  * Errors: LB_E_INVALID, LB_E_CUDA. */
 lb_status lb_free_energy_noalloc(const lb_params *p, const void *f_dev, double *out_dev);
 
+/* ---- adjoint rollout -----------------------------------------------------------------
+ * Reverse-mode gradients of a loss of the final densities with respect to the initial
+ * densities and the mixture parameters a, kappa, b, through the hand-written transpose
+ * of the fused timestep (FP64 contexts, "log" force).  Long rollouts keep a copy of the
+ * state every ckpt_every steps and recompute each segment during the backward pass. */
+
+/* Advance nsteps >= 1 FP64 timesteps from the current state (which must come from
+ * lb_init_fields with mom = NULL for rho_bar_0 below to be the gradient with respect to
+ * the initial densities), keeping (nsteps / ckpt_every + 1) device checkpoints.
+ * Errors: LB_E_INVALID (not FP64 / not the log force), LB_E_STATE, LB_E_NOMEM, LB_E_CUDA. */
+lb_status lb_rollout_forward(lb_ctx *ctx, int64_t nsteps, int32_t ckpt_every);
+
+/* Given rho_bar_T = dL/d rho at the end of the recorded rollout (host [c][y][x]), return
+ * rho_bar_0 = dL/d rho_0 (host [c][y][x], may be NULL) and grad (host, may be NULL) =
+ * [dL/da_cd (ncomp x ncomp, each entry taken as independent), dL/dkappa_cd (ncomp x ncomp),
+ * dL/db_c (ncomp)].  For a symmetric pair a_12 = a_21 the gradient of the shared value is
+ * the sum of the two entries.  Allocates ckpt_every states plus work arrays (FP64) for the
+ * duration of the call; synchronises.  Errors: LB_E_INVALID, LB_E_STATE (no rollout),
+ * LB_E_NOMEM, LB_E_CUDA. */
+lb_status lb_rollout_backward(lb_ctx *ctx, const double *rho_bar_T, double *rho_bar_0, double *grad);
+
+/* ---- batched independent runs (a phase-diagram sweep) --------------------------------
+ * Many independent runs that share the mixture (ncomp, a, b, kappa, lambda, tau, force
+ * method, precision) but differ in lattice, size, kT and gamma_mu advance together on
+ * one GPU.  Every run follows exactly the arithmetic of the same run advanced alone
+ * through lb_create/lb_step (bitwise equal results).  D2Q9 runs: one kernel launch per
+ * timestep over a flat list of tiles of all runs.  D1Q3 runs (2 <= nx <= 4096): one CTA
+ * per run holds the whole run in shared memory for a chunk of timesteps.  lb_batch_step
+ * replays CUDA graphs of 32-timestep chunks. */
+typedef struct {
+    int32_t lattice;  /* LB_D1Q3 (ny = 1, 2 <= nx <= 4096) or LB_D2Q9 (nx, ny >= 2) */
+    int32_t nx, ny;
+    double kT;        /* this run's thermodynamic temperature */
+    double gamma_mu;  /* this run's gamma_mu */
+} lb_run_desc;
+
+typedef struct lb_batch lb_batch;
+
+/* Create a batch: shared->{abi, ncomp, precision, force_method, tau, a, kappa, lambda, b,
+ * rho_ref, device, stream, tile_x, tile_y} apply to every run (tile: D2Q9 tile, 0 = 32x8;
+ * lattice, nx, ny, kT, gamma_mu are taken from runs[]).  Allocates pooled buffers with
+ * cudaMalloc.  Errors: LB_E_INVALID (bad run, D1Q3 run too long for shared memory),
+ * LB_E_NOMEM, LB_E_CUDA. */
+lb_status lb_batch_create(const lb_params *shared, const lb_run_desc *runs, int32_t nruns, lb_batch **out);
+
+/* Equilibrium at rest of host densities: rho_all holds the runs one after another, each
+ * in the layout [c][y][x].  Synchronous; clears the per-run error flags.
+ * Errors: LB_E_INVALID, LB_E_DOMAIN (a density <= 0 or eta <= 0), LB_E_CUDA. */
+lb_status lb_batch_init(lb_batch *b, const double *rho_all);
+
+/* Enqueue nsteps timesteps of every run on the batch stream (asynchronous). */
+lb_status lb_batch_step(lb_batch *b, int64_t nsteps);
+
+/* Densities [c][y][x] and bare momenta [c][d][y][x] (may be NULL) of one run; synchronises. */
+lb_status lb_batch_read(lb_batch *b, int32_t run, double *rho, double *mom);
+
+/* Per-run error words (bit 0: a density or eta <= 0 or a non-finite value was met);
+ * flags[nruns]; synchronises.  A failed run does not stop the others. */
+lb_status lb_batch_errors(lb_batch *b, uint32_t *flags);
+
+/* Select the D2Q9 tile (32x8, 64x4, 32x16 or 64x8); drops the captured graphs. */
+lb_status lb_batch_set_tile(lb_batch *b, int32_t tile_x, int32_t tile_y);
+
+/* Advance nsteps timesteps and return their device time in ms (CUDA events on the batch
+ * stream; synchronises).  Used by the tile autotuner. */
+lb_status lb_batch_time_steps(lb_batch *b, int32_t nsteps, double *ms);
+
+int64_t lb_batch_step_count(const lb_batch *b);
+int64_t lb_batch_launch_count(const lb_batch *b);
+const char *lb_batch_last_error(const lb_batch *b);
+lb_status lb_batch_destroy(lb_batch *b);
+
 /* Size in bytes of a saved state, and save/load of the raw populations
  * ([c][i][y][x] in the storage type of the precision, plus a 64-byte header with the
  * step counter and a parameter hash).  lb_save_state synchronises; lb_load_state

@@ -35,6 +35,7 @@ SEED_BASE = 1805072510
 SWEEP_SEED_BASE = 1805072600
 _HERE = os.path.dirname(os.path.abspath(__file__))
 PARAMS_JSON = os.path.join(_HERE, "params.json")
+SWEEP_JSON = os.path.join(_HERE, "sweep.json")
 
 
 def seed(k):
@@ -154,3 +155,58 @@ def lib_kwargs(p, **over):
               kT=p["kT"], gamma_mu=p["gamma_mu"], a=p["a"], kappa=p["kappa"], lam=p["lam"], b=p["b"])
     kw.update(over)
     return kw
+
+
+# --------------------------------------------------------------------------- sweep (c3)
+
+def sweep_runs(n_d1=256, n_d2=128, with_phases=True):
+    """Run records of the batched sweep: lattice, size, x (mole fraction of A), kT and, when
+    the stored file exists, the coexisting phases and gamma_mu (sweep.json)."""
+    p = base_params("c1")
+    a, b = p["a"], p["b"]
+    stored = None
+    if with_phases and os.path.exists(SWEEP_JSON):
+        with open(SWEEP_JSON) as fh:
+            stored = json.load(fh)
+    runs = []
+    for r in range(n_d1 + n_d2):
+        g = np.random.default_rng(SWEEP_SEED_BASE + r)
+        if r < n_d1:
+            L = int(g.integers(128, 4097))
+            rec = dict(lattice="D1Q3", nx=L, ny=1)
+        else:
+            side = int(g.integers(64, 513))
+            rec = dict(lattice="D2Q9", nx=side, ny=side)
+        x = float(g.uniform(0.05, 0.95))
+        frac = float(g.uniform(0.6, 0.98))
+        rec["x"] = x
+        rec["kT"] = frac * one_fluid_critical_kT(a, b, [x, 1 - x])
+        rec["kT_frac"] = frac
+        rec["seed"] = SWEEP_SEED_BASE + r
+        if stored is not None and r < len(stored):
+            rec.update(stored[r])
+        runs.append(rec)
+    return runs
+
+
+def sweep_fields(rec):
+    """Seeded initial densities [c][y][x] of one sweep run: a slab of the liquid phase
+    between tanh edges (width 2) in the gas phase, sized by the lever rule so that the
+    mean is rec['mean'], plus uniform noise in +-1e-3; one-phase runs: the mean plus noise."""
+    g = np.random.default_rng(rec["seed"] + 10 ** 6)
+    nx, ny = rec["nx"], rec["ny"]
+    mean = np.asarray(rec["mean"])
+    if "liquid" in rec:
+        gas, liq = np.asarray(rec["gas"]), np.asarray(rec["liquid"])
+        phi = float((mean.sum() - gas.sum()) / (liq.sum() - gas.sum()))
+        phi = min(max(phi, 0.1), 0.9)
+        xs = np.arange(nx, dtype=np.float64)
+        lo = nx * (0.5 - phi / 2) - 0.5
+        hi = nx * (0.5 + phi / 2) - 0.5
+        s = 0.5 * (np.tanh((xs - lo) / 2.0) - np.tanh((xs - hi) / 2.0))
+        rho = np.stack([gas[c] + (liq[c] - gas[c]) * s for c in range(2)])[:, None, :]
+        rho = np.broadcast_to(rho, (2, ny, nx)).copy()
+    else:
+        rho = np.broadcast_to(mean.reshape(2, 1, 1), (2, ny, nx)).copy()
+    rho += g.uniform(-1e-3, 1e-3, size=rho.shape)
+    return np.ascontiguousarray(rho)

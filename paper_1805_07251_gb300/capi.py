@@ -23,6 +23,16 @@ LB_FP64, LB_FP32_MIXED, LB_FP32_DFMU = 0, 1, 2
 LB_FORCE_LOG, LB_FORCE_NID = 0, 1
 
 
+class lb_run_desc(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int32),
+        ("nx", ctypes.c_int32),
+        ("ny", ctypes.c_int32),
+        ("kT", ctypes.c_double),
+        ("gamma_mu", ctypes.c_double),
+    ]
+
+
 class lb_params(ctypes.Structure):
     _fields_ = [
         ("abi", ctypes.c_uint32),
@@ -88,6 +98,17 @@ def load():
         "lb_last_error": (ctypes.c_char_p, [C]),
         "lb_selftest_log": (ctypes.c_int, [ctypes.c_int32, _DP, ctypes.c_int64, _DP, _DP, _DP]),
         "lb_free_energy_noalloc": (ctypes.c_int, [P, C, C]),
+        "lb_batch_create": (ctypes.c_int, [P, ctypes.POINTER(lb_run_desc), ctypes.c_int32, ctypes.POINTER(C)]),
+        "lb_batch_init": (ctypes.c_int, [C, _DP]),
+        "lb_batch_step": (ctypes.c_int, [C, ctypes.c_int64]),
+        "lb_batch_read": (ctypes.c_int, [C, ctypes.c_int32, _DP, _DP]),
+        "lb_batch_errors": (ctypes.c_int, [C, ctypes.POINTER(ctypes.c_uint32)]),
+        "lb_batch_set_tile": (ctypes.c_int, [C, ctypes.c_int32, ctypes.c_int32]),
+        "lb_batch_time_steps": (ctypes.c_int, [C, ctypes.c_int32, _DP]),
+        "lb_batch_step_count": (ctypes.c_int64, [C]),
+        "lb_batch_launch_count": (ctypes.c_int64, [C]),
+        "lb_batch_last_error": (ctypes.c_char_p, [C]),
+        "lb_batch_destroy": (ctypes.c_int, [C]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -207,3 +228,64 @@ def lb_free_energy_noalloc(p, f_ptr, out_ptr):
     rc = load().lb_free_energy_noalloc(ctypes.byref(p), ctypes.c_void_p(f_ptr), ctypes.c_void_p(out_ptr))
     if rc != LB_OK:
         raise LBError(rc, "lb_free_energy_noalloc")
+
+
+# --- batched runs -------------------------------------------------------------
+
+def _bcheck(b, rc, what):
+    if rc != LB_OK:
+        msg = load().lb_batch_last_error(b).decode() if b else ""
+        raise LBError(rc, f"{what}: {msg}")
+
+
+def lb_batch_create(shared, runs):
+    """runs: sequence of (lattice, nx, ny, kT, gamma_mu)."""
+    arr = (lb_run_desc * len(runs))()
+    for k, (lat, nx, ny, kT, g) in enumerate(runs):
+        arr[k].lattice, arr[k].nx, arr[k].ny, arr[k].kT, arr[k].gamma_mu = int(lat), int(nx), int(ny), kT, g
+    out = ctypes.c_void_p()
+    rc = load().lb_batch_create(ctypes.byref(shared), arr, len(runs), ctypes.byref(out))
+    if rc != LB_OK:
+        raise LBError(rc, "lb_batch_create rejected the runs")
+    return out
+
+
+def lb_batch_init(b, rho_all):
+    rho_all = np.ascontiguousarray(rho_all, dtype=np.float64)
+    _bcheck(b, load().lb_batch_init(b, _dp(rho_all)), "lb_batch_init")
+
+
+def lb_batch_step(b, nsteps):
+    _bcheck(b, load().lb_batch_step(b, int(nsteps)), "lb_batch_step")
+
+
+def lb_batch_read(b, run, rho_out, mom_out=None):
+    _bcheck(b, load().lb_batch_read(b, int(run), _dp(rho_out), _dp(mom_out)), "lb_batch_read")
+
+
+def lb_batch_errors(b, nruns):
+    flags = (ctypes.c_uint32 * nruns)()
+    _bcheck(b, load().lb_batch_errors(b, flags), "lb_batch_errors")
+    return np.array(flags[:], dtype=np.uint32)
+
+
+def lb_batch_set_tile(b, tx, ty):
+    _bcheck(b, load().lb_batch_set_tile(b, int(tx), int(ty)), "lb_batch_set_tile")
+
+
+def lb_batch_time_steps(b, nsteps):
+    ms = np.zeros(1)
+    _bcheck(b, load().lb_batch_time_steps(b, int(nsteps), _dp(ms)), "lb_batch_time_steps")
+    return float(ms[0])
+
+
+def lb_batch_step_count(b):
+    return int(load().lb_batch_step_count(b))
+
+
+def lb_batch_launch_count(b):
+    return int(load().lb_batch_launch_count(b))
+
+
+def lb_batch_destroy(b):
+    load().lb_batch_destroy(b)

@@ -12,26 +12,7 @@
 
 using namespace lbvdw;
 
-struct lb_ctx {
-    lb_params p;
-    int Q = 0, D = 0;
-    size_t n = 0;      // nodes
-    size_t elem = 0;   // bytes per stored population
-    void *f[2] = {nullptr, nullptr};
-    int cur = 0;
-    double *rho = nullptr;  // moments scratch [N][n]
-    double *mom = nullptr;  // moments scratch [N][D][n]
-    double *partial = nullptr;
-    int nparts = 0;
-    double *diag = nullptr;  // [N + 3]
-    unsigned *err = nullptr;
-    LogTables *tbl = nullptr;  // device copy of the log tables
-    cudaStream_t stream = nullptr;
-    DevParams dp{};
-    int64_t steps = 0, launches = 0;
-    bool has_state = false, poisoned = false;
-    std::string msg;
-};
+#include "lb_ctx.cuh"
 
 namespace {
 
@@ -194,6 +175,41 @@ void fill_log_tables(LogTables *t) {
     t->ln2_lo_f = (float)(ln2 - (long double)t->ln2_hi_f);
 }
 
+// Kernel parameter block of a parameter set (FP64 values, their FP32 and double-float
+// copies, Psi coefficients); reference densities start at zero (set by the init call).
+void make_dev_params(const lb_params &p, DevParams &d, unsigned *err, const LogTables *tbl) {
+    d = DevParams{};
+    d.nx = p.nx;
+    d.ny = p.ny;
+    d.omega = 1.0 / p.tau;
+    d.psi_g = (p.tau - 0.25) / p.tau;
+    d.psi_l = 1.0 / (12.0 * p.tau);
+    d.kT = p.kT;
+    d.gamma = p.gamma_mu;
+    for (int k = 0; k < 16; ++k) {
+        d.a[k] = p.a[k];
+        d.kappa[k] = p.kappa[k];
+        d.lam[k] = p.lambda[k];
+        d.a2_f[k] = (float)(2.0 * p.a[k]);
+        d.kappa_f[k] = (float)p.kappa[k];
+        d.lam_f[k] = (float)p.lambda[k];
+    }
+    for (int k = 0; k < 4; ++k) {
+        d.b[k] = p.b[k];
+        d.rho_ref[k] = 0.0;
+        d.rho_ref_f[k] = 0.0f;
+        split_float(p.b[k], d.b_hi[k], d.b_lo[k]);
+    }
+    d.err = err;
+    d.tbl = tbl;
+    d.gkT = p.gamma_mu * p.kT;
+    split_float(d.gkT, d.gkT_hi, d.gkT_lo);
+    split_float(p.gamma_mu, d.gamma_hi, d.gamma_lo);
+    d.omega_f = (float)d.omega;
+    d.psi_g_f = (float)d.psi_g;
+    d.psi_l_f = (float)d.psi_l;
+}
+
 }  // namespace lbvdw
 
 extern "C" {
@@ -276,29 +292,7 @@ lb_status lb_create(const lb_params *p, lb_ctx **out) {
         lb_destroy(c);
         return LB_E_NOMEM;
     }
-    DevParams &d = c->dp;
-    d.nx = p->nx;
-    d.ny = p->ny;
-    d.omega = 1.0 / p->tau;
-    d.psi_g = (p->tau - 0.25) / p->tau;
-    d.psi_l = 1.0 / (12.0 * p->tau);
-    d.kT = p->kT;
-    d.gamma = p->gamma_mu;
-    for (int k = 0; k < 16; ++k) {
-        d.a[k] = p->a[k];
-        d.kappa[k] = p->kappa[k];
-        d.lam[k] = p->lambda[k];
-    }
-    for (int k = 0; k < 4; ++k) {
-        d.b[k] = p->b[k];
-        d.rho_ref[k] = 0.0;
-    }
-    d.err = c->err;
-    d.tbl = c->tbl;
-    d.gkT = p->gamma_mu * p->kT;
-    for (int k = 0; k < 4; ++k) split_float(p->b[k], d.b_hi[k], d.b_lo[k]);
-    split_float(d.gkT, d.gkT_hi, d.gkT_lo);
-    split_float(p->gamma_mu, d.gamma_hi, d.gamma_lo);
+    make_dev_params(*p, c->dp, c->err, c->tbl);
     LogTables h;
     fill_log_tables(&h);
     if (cudaMemcpy(c->tbl, &h, sizeof h, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -318,6 +312,7 @@ static lb_status init_common(lb_ctx *c, const double *rho_dev, const double *mom
     if (c->p.precision != LB_FP64)
         for (int k = 0; k < N; ++k)
             c->dp.rho_ref[k] = (double)(float)(c->p.rho_ref[k] > 0.0 ? c->p.rho_ref[k] : rho_ref[k]);
+    for (int k = 0; k < 4; ++k) c->dp.rho_ref_f[k] = (float)c->dp.rho_ref[k];
     LB_CUDA(c, cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
     c->cur = 0;
     FieldLaunch a = field_args(c);
@@ -330,6 +325,7 @@ static lb_status init_common(lb_ctx *c, const double *rho_dev, const double *mom
     c->steps = 0;
     c->has_state = true;
     c->poisoned = false;
+    c->rollout_steps = -1;
     c->msg.clear();
     return LB_OK;
 }
@@ -529,6 +525,7 @@ lb_status lb_destroy(lb_ctx *c) {
     cudaFree(c->diag);
     cudaFree(c->err);
     cudaFree(c->tbl);
+    for (double *q : c->ckpt) cudaFree(q);
     delete c;
     return LB_OK;
 }

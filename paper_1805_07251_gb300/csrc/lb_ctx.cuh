@@ -1,0 +1,34 @@
+// lb_ctx.cuh -- the context behind lb_ctx* (private to the library).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "lb_launch.cuh"
+#include "lbvdw.h"
+
+struct lb_ctx {
+    // checkpointed rollout for the adjoint (lb_rollout_*): FP64 copies of the state every
+    // ckpt_every steps, and the number of steps recorded
+    std::vector<double *> ckpt;
+    int ckpt_every = 0;
+    int64_t rollout_steps = -1;
+    lb_params p;
+    int Q = 0, D = 0;
+    size_t n = 0;      // nodes
+    size_t elem = 0;   // bytes per stored population
+    void *f[2] = {nullptr, nullptr};
+    int cur = 0;
+    double *rho = nullptr;  // moments scratch [N][n]
+    double *mom = nullptr;  // moments scratch [N][D][n]
+    double *partial = nullptr;
+    int nparts = 0;
+    double *diag = nullptr;  // [N + 3]
+    unsigned *err = nullptr;
+    lbvdw::LogTables *tbl = nullptr;  // device copy of the log tables
+    cudaStream_t stream = nullptr;
+    lbvdw::DevParams dp{};
+    int64_t steps = 0, launches = 0;
+    bool has_state = false, poisoned = false;
+    std::string msg;
+};
+

@@ -38,7 +38,25 @@ struct DevParams {
     double gkT;         // gamma_mu * kT
     float b_hi[4], b_lo[4];  // double-float copies of b, gamma kT and gamma
     float gkT_hi, gkT_lo, gamma_hi, gamma_lo;
+    // FP32 copies for the FP32 paths (no double->float conversion in the kernels)
+    float a2_f[16], kappa_f[16], lam_f[16];  // 2 a, kappa, lambda
+    float rho_ref_f[4], omega_f, psi_g_f, psi_l_f;
 };
+
+// a parameter in the compute type R: the double value or its precomputed float copy
+template <class R>
+__device__ __forceinline__ R pv(double d, float f);
+template <>
+__device__ __forceinline__ double pv<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float pv<float>(double, float f) { return f; }
+
+// 1/x in the compute type: exact division in FP64, MUFU reciprocal in FP32
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+
+// periodic wrap of g in [-n, 2n)
+__device__ __forceinline__ int wrap1(int g, int n) { return g < 0 ? g + n : (g >= n ? g - n : g); }
 
 // ---------------------------------------------------------------------------
 // lattices.  D1Q3: v = 0, +1, -1 (Sec. V), w = 2/3, 1/6, 1/6 (the weights of the
@@ -143,9 +161,244 @@ __device__ __forceinline__ void grad_phi(const T *s, int mx, int my, int MXW, R 
     }
 }
 
+// shared-memory log tables of the MU variant (TBL_WORDS floats)
+template <int MU>
+struct TblWords {
+    static constexpr int value = MU == MU_TBL ? 3 * LOG_TBL * 2 : (MU == MU_DF ? 3 * LOG_TBL : 1);
+};
+
+template <int MU>
+__device__ __forceinline__ void load_tables(float *s_tbl, const DevParams &P, int tid, int nt) {
+    if constexpr (MU == MU_TBL) {
+        double *t = reinterpret_cast<double *>(s_tbl);
+        for (int k = tid; k < LOG_TBL; k += nt) {
+            t[k] = P.tbl->r64[k];
+            t[LOG_TBL + k] = P.tbl->t64_hi[k];
+            t[2 * LOG_TBL + k] = P.tbl->t64_lo[k];
+        }
+    } else if constexpr (MU == MU_DF) {
+        for (int k = tid; k < LOG_TBL; k += nt) {
+            s_tbl[k] = P.tbl->r32[k];
+            s_tbl[LOG_TBL + k] = P.tbl->t32_hi[k];
+            s_tbl[2 * LOG_TBL + k] = P.tbl->t32_lo[k];
+        }
+    }
+}
+
+// One node of phase 2: phi^c = gamma mu^c (minus theta ln rho^c for "nid") from the
+// densities r and the linear part lin = sum_c' (2 a rho' + kappa Lap rho').
+// Returns false when rho^c <= 0 or eta <= 0 (phi is then meaningless).
+template <int N, class R, int FORCE, int MU>
+__device__ __forceinline__ bool mu_node(const R (&r)[N], const R (&lin)[N], const DevParams &P,
+                                        const float *s_tbl, typename MuStore<MU>::T (&phi)[N]) {
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < N; ++c) ok = ok && (r[c] > (R)0);
+    if constexpr (MU == MU_F64) {
+        double eta = 1.0, rt = 0.0;
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            eta -= P.b[c] * r[c];
+            rt += r[c];
+        }
+        ok = ok && eta > 0.0;
+        const double ieta = 1.0 / eta;
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            double m = P.kT * (log(r[c] * ieta) + P.b[c] * rt * ieta) - lin[c];
+            double ph = P.gamma * m;
+            if constexpr (FORCE == 1) ph -= (1.0 / 3.0) * log(r[c]);
+            phi[c] = ph;
+        }
+    } else if constexpr (MU == MU_TBL) {
+        const double *t = reinterpret_cast<const double *>(s_tbl);
+        double eta = 1.0, rt = 0.0;
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            eta = fma(-P.b[c], (double)r[c], eta);
+            rt += (double)r[c];
+        }
+        ok = ok && eta > 0.0;
+        double y = (double)__frcp_rn((float)eta);  // Newton: y <- y + y (1 - eta y), twice
+        y = fma(y, fma(-eta, y, 1.0), y);
+        y = fma(y, fma(-eta, y, 1.0), y);
+        const double rte = rt * y;
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            double lg = ok ? log64_tbl((double)r[c] * y, t, t + LOG_TBL, t + 2 * LOG_TBL, P.tbl->ln2_hi_d,
+                                       P.tbl->ln2_lo_d)
+                           : 0.0;
+            double ph = fma(P.gkT, fma(P.b[c], rte, lg), -P.gamma * (double)lin[c]);
+            if constexpr (FORCE == 1)
+                ph -= (1.0 / 3.0) * (ok ? log64_tbl((double)r[c], t, t + LOG_TBL, t + 2 * LOG_TBL, P.tbl->ln2_hi_d,
+                                                     P.tbl->ln2_lo_d)
+                                        : 0.0);
+            phi[c] = ph;
+        }
+    } else {  // MU_DF
+        df eta = {1.0f, 0.0f}, rt = {0.0f, 0.0f};
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            eta = df_add(eta, df_neg(df_mul_f({P.b_hi[c], P.b_lo[c]}, r[c])));
+            rt = df_add(rt, {r[c], 0.0f});
+        }
+        ok = ok && eta.hi > 0.0f;
+        const df ieta = df_recip(eta);
+        const df rte = df_mul(rt, ieta);
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            df lg = ok ? df_log(df_mul_f(ieta, r[c]), s_tbl, s_tbl + LOG_TBL, s_tbl + 2 * LOG_TBL, P.tbl->ln2_hi_f,
+                                P.tbl->ln2_lo_f)
+                       : df{0.0f, 0.0f};
+            df m = df_add(lg, df_mul(rte, {P.b_hi[c], P.b_lo[c]}));
+            df ph = df_add(df_mul(m, {P.gkT_hi, P.gkT_lo}), df_neg(df_mul_f({P.gamma_hi, P.gamma_lo}, lin[c])));
+            if constexpr (FORCE == 1) {
+                df lr = ok ? df_log({r[c], 0.0f}, s_tbl, s_tbl + LOG_TBL, s_tbl + 2 * LOG_TBL, P.tbl->ln2_hi_f,
+                                    P.tbl->ln2_lo_f)
+                           : df{0.0f, 0.0f};
+                ph = df_add(ph, df_neg(df_mul_f(lr, 1.0f / 3.0f)));
+            }
+            phi[c] = ph;
+        }
+    }
+    return ok;
+}
+
+// One node of phase 3: from rho, Lap rho, D phi, D rho (log force) and the bare momenta,
+// the total gain G (mean field + implicit friction), then Psi, the forcing populations
+// and the BGK collision.  g holds the node's stored populations (deviations); post
+// receives the post-collision deviations in the same order.
+template <int LAT, int N, class R, int FORCE>
+__device__ __forceinline__ void collide_node(const R (&rho)[N], const R (&lap)[N], const R (&gpx)[N],
+                                             const R (&gpy)[N], const R (&grx)[N], const R (&gry)[N],
+                                             const R (&jx)[N], const R (&jy)[N], const DevParams &P,
+                                             const R (&g)[N][Lat<LAT>::Q], R (&post)[N][Lat<LAT>::Q]) {
+    using L = Lat<LAT>;
+    constexpr int Q = L::Q;
+    R ux[N], uy[N], Gx[N], Gy[N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        if constexpr (FORCE == 0) {
+            Gx[c] = -rho[c] * gpx[c] + (R)(1.0 / 3.0) * grx[c];
+            Gy[c] = -rho[c] * gpy[c] + (R)(1.0 / 3.0) * gry[c];
+        } else {
+            Gx[c] = -rho[c] * gpx[c];
+            Gy[c] = -rho[c] * gpy[c];
+        }
+        const R ir = rcp(rho[c]);
+        ux[c] = jx[c] * ir;
+        uy[c] = jy[c] * ir;
+    }
+
+    // friction with the implicit u-hat: (D + L/2) h = -L u0, G^f = D h  (per direction)
+    if constexpr (N > 1) {
+        R W[N][N];
+#pragma unroll
+        for (int c = 0; c < N; ++c)
+#pragma unroll
+            for (int cc = 0; cc < N; ++cc)
+                W[c][cc] = (c == cc) ? (R)0
+                                     : pv<R>(P.lam[c * 4 + cc], P.lam_f[c * 4 + cc]) * rho[c] * rho[cc] *
+                                           rcp(rho[c] + rho[cc]);
+#pragma unroll
+        for (int d = 0; d < L::D; ++d) {
+            R u0[N], M[N][N], h[N];
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                R uu = d == 0 ? ux[c] : uy[c];
+                R gg = d == 0 ? Gx[c] : Gy[c];
+                u0[c] = uu + (R)0.5 * gg * rcp(rho[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                R diag = rho[c], rhs = (R)0;
+#pragma unroll
+                for (int cc = 0; cc < N; ++cc) {
+                    M[c][cc] = (R)(-0.5) * W[c][cc];
+                    diag += (R)0.5 * W[c][cc];
+                    rhs -= W[c][cc] * (u0[c] - u0[cc]);
+                }
+                M[c][c] = diag;
+                h[c] = rhs;
+            }
+            // symmetric positive definite: elimination without pivoting
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                R inv = rcp(M[k][k]);
+#pragma unroll
+                for (int r2 = k + 1; r2 < N; ++r2) {
+                    R m = M[r2][k] * inv;
+#pragma unroll
+                    for (int c2 = k + 1; c2 < N; ++c2) M[r2][c2] -= m * M[k][c2];
+                    h[r2] -= m * h[k];
+                }
+            }
+#pragma unroll
+            for (int k = N - 1; k >= 0; --k) {
+                R sacc = h[k];
+#pragma unroll
+                for (int c2 = k + 1; c2 < N; ++c2) sacc -= M[k][c2] * h[c2];
+                h[k] = sacc * rcp(M[k][k]);
+            }
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                if (d == 0) Gx[c] += rho[c] * h[c];
+                else Gy[c] += rho[c] * h[c];
+            }
+        }
+    }
+
+    const R omega = pv<R>(P.omega, P.omega_f), cg = pv<R>(P.psi_g, P.psi_g_f), cl = pv<R>(P.psi_l, P.psi_l_f);
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        const R r = rho[c], u = ux[c], v = uy[c], gx = Gx[c], gy = Gy[c];
+        const R ir = rcp(r);
+        // second forcing moment S = G u + u G - Psi, -Psi = cg G G / rho + cl Lap rho I
+        const R Sxx = (R)2 * gx * u + cg * gx * gx * ir + cl * lap[c];
+        const R Syy = (R)2 * gy * v + cg * gy * gy * ir + cl * lap[c];
+        const R Sxy = gx * v + u * gy + cg * gx * gy * ir;
+        const R usq = u * u + v * v;
+        const R drho = r - pv<R>(P.rho_ref[c], P.rho_ref_f[c]);
+        // Directions come in opposite pairs (i, i'): v.u, v.G flip sign, S:(vv - theta I)
+        // does not.  With A = w (drho + rho (4.5 (v.u)^2 - 1.5 u^2)), B = 3 w rho v.u,
+        // C = 4.5 w S:(vv - theta I), D = 3 w v.G:  f^eq - w rho_ref = A +- B, F = C +- D.
+        const R third = (R)(1.0 / 3.0);
+        {
+            const R w0 = (R)L::w(0);
+            const R A0 = w0 * (drho - (R)1.5 * r * usq);
+            R SQ0 = -third * Sxx;
+            if constexpr (LAT == 2) SQ0 -= third * Syy;
+            const R C0 = (R)4.5 * w0 * SQ0;
+            post[c][0] = g[c][0] + omega * (A0 - g[c][0]) + C0;
+        }
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const int cx = L::vx(i), cy = L::vy(i);
+            // handle each pair once, from its member with the smaller index
+            int ip = 0;
+#pragma unroll
+            for (int k = 1; k < Q; ++k)
+                if (L::vx(k) == -cx && L::vy(k) == -cy) ip = k;
+            if (ip < i) continue;
+            const R wi = (R)L::w(i);
+            const R vu = (R)cx * u + (R)cy * v;
+            const R vG = (R)cx * gx + (R)cy * gy;
+            R SQ = Sxx * ((R)(cx * cx) - third);
+            if constexpr (LAT == 2) SQ += Syy * ((R)(cy * cy) - third) + (R)2 * Sxy * (R)(cx * cy);
+            const R A = wi * (drho + r * ((R)4.5 * vu * vu - (R)1.5 * usq));
+            const R B = (R)3 * wi * r * vu;
+            const R C = (R)4.5 * wi * SQ;
+            const R D = (R)3 * wi * vG;
+            post[c][i] = g[c][i] + omega * (A + B - g[c][i]) + (C + D);
+            post[c][ip] = g[c][ip] + omega * (A - B - g[c][ip]) + (C - D);
+        }
+    }
+}
+
+// The fused step on one TX x TY tile with origin (x0, y0) of the lattice described by P.
 template <int LAT, int N, int TX, int TY, class S, class R, int FORCE, int MU>
-__global__ void __launch_bounds__(TX *TY)
-    lb_step_kernel(const S *__restrict__ fin, S *__restrict__ fout, DevParams P) {
+__device__ __forceinline__ void step_tile(const S *__restrict__ fin, S *__restrict__ fout, const DevParams &P,
+                                          int x0, int y0) {
     using L = Lat<LAT>;
     using MT = typename MuStore<MU>::T;
     constexpr int Q = L::Q;
@@ -160,43 +413,32 @@ __global__ void __launch_bounds__(TX *TY)
 
     __shared__ R s_rho[N][EY * EX];
     __shared__ MT s_phi[N][MY * MX];  // gamma mu (log) or gamma mu - theta ln rho (nid)
-    constexpr int TBL_WORDS = MU == MU_TBL ? 3 * LOG_TBL * 2 : (MU == MU_DF ? 3 * LOG_TBL : 1);
-    __shared__ __align__(16) float s_tbl[TBL_WORDS];
+    __shared__ __align__(16) float s_tbl[TblWords<MU>::value];
 
     const int nx = P.nx, ny = P.ny;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = tx + TX * ty;
     const int x = x0 + tx, y = y0 + ty;
     const bool inside = x < nx && y < ny;
-
-    if constexpr (MU == MU_TBL) {
-        double *t = reinterpret_cast<double *>(s_tbl);
-        for (int k = tid; k < LOG_TBL; k += NT) {
-            t[k] = P.tbl->r64[k];
-            t[LOG_TBL + k] = P.tbl->t64_hi[k];
-            t[2 * LOG_TBL + k] = P.tbl->t64_lo[k];
-        }
-    } else if constexpr (MU == MU_DF) {
-        for (int k = tid; k < LOG_TBL; k += NT) {
-            s_tbl[k] = P.tbl->r32[k];
-            s_tbl[LOG_TBL + k] = P.tbl->t32_hi[k];
-            s_tbl[2 * LOG_TBL + k] = P.tbl->t32_lo[k];
-        }
-    }
+    load_tables<MU>(s_tbl, P, tid, NT);
 
     // ---- phase 1a: own node -> registers, rho^c -> shared -------------------
+    const size_t plane = (size_t)nx * (size_t)ny;
+    // lattices at least a tile plus its ring wide wrap with one conditional add
+    const bool small = nx <= TX + 1 || (LAT == 2 && ny <= TY + 1);
     S g[KEEP ? N : 1][KEEP ? Q : 1];
     R jx[N], jy[N];
     {
-        const int gx = inside ? x : wrap(x, nx), gy = inside ? y : (LAT == 1 ? 0 : wrap(y, ny));
+        const int gx = small ? wrap(x, nx) : wrap1(x, nx);
+        const int gy = LAT == 1 ? 0 : (small ? wrap(y, ny) : wrap1(y, ny));
+        const S *src = fin + (size_t)gy * nx + gx;
         const int ex = tx + 2, ey = ty + 2 * HY;
 #pragma unroll
         for (int c = 0; c < N; ++c) {
             R acc = (R)0, ax = (R)0, ay = (R)0;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                S v = fin[pop_index(c, i, Q, gy, gx, nx, ny)];
+                S v = src[(size_t)(c * Q + i) * plane];
                 if constexpr (KEEP) g[c][i] = v;
                 R rv = (R)v;
                 acc += rv;
@@ -205,7 +447,7 @@ __global__ void __launch_bounds__(TX *TY)
                 if (L::vy(i) == 1) ay += rv;
                 if (L::vy(i) == -1) ay -= rv;
             }
-            s_rho[c][ey * EX + ex] = (R)P.rho_ref[c] + acc;
+            s_rho[c][ey * EX + ex] = pv<R>(P.rho_ref[c], P.rho_ref_f[c]) + acc;
             jx[c] = ax;
             jy[c] = ay;
         }
@@ -231,107 +473,42 @@ __global__ void __launch_bounds__(TX *TY)
                 ex = col < 2 ? col : EX - 4 + col;
             }
         }
-        const int gx = wrap(x0 + ex - 2, nx);
-        const int gy = (LAT == 1) ? 0 : wrap(y0 + ey - 2, ny);
+        const int gx = small ? wrap(x0 + ex - 2, nx) : wrap1(x0 + ex - 2, nx);
+        const int gy = (LAT == 1) ? 0 : (small ? wrap(y0 + ey - 2, ny) : wrap1(y0 + ey - 2, ny));
+        const S *src = fin + (size_t)gy * nx + gx;
 #pragma unroll
         for (int c = 0; c < N; ++c) {
             R acc = (R)0;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) acc += (R)fin[pop_index(c, i, Q, gy, gx, nx, ny)];
-            s_rho[c][ey * EX + ex] = (R)P.rho_ref[c] + acc;
+            for (int i = 0; i < Q; ++i) acc += (R)src[(size_t)(c * Q + i) * plane];
+            s_rho[c][ey * EX + ex] = pv<R>(P.rho_ref[c], P.rho_ref_f[c]) + acc;
         }
     }
     __syncthreads();
 
-    // ---- phase 2: phi^c = gamma mu^c (- theta ln rho^c for "nid") on tile + 1 --
+    // ---- phase 2: phi^c on tile + 1 ring --------------------------------------
     unsigned bad = 0;
     for (int k = tid; k < MX * MY; k += NT) {
         const int mx = k % MX, my = k / MX;
         const int ex = mx + 1, ey = my + HY;
         R r[N], lin[N];
-        bool ok = true;
 #pragma unroll
         for (int c = 0; c < N; ++c) {
             r[c] = s_rho[c][ey * EX + ex];
-            ok = ok && (r[c] > (R)0);
+            lin[c] = (R)0;
         }
-        // linear part sum_c' (2 a rho' + kappa Lap rho'), in R
-#pragma unroll
-        for (int c = 0; c < N; ++c) lin[c] = (R)0;
 #pragma unroll
         for (int cc = 0; cc < N; ++cc) {
             R lp = lap_at<LAT, R>(s_rho[cc], ex, ey, EX);
 #pragma unroll
-            for (int c = 0; c < N; ++c) lin[c] += (R)(2.0 * P.a[c * 4 + cc]) * r[cc] + (R)P.kappa[c * 4 + cc] * lp;
+            for (int c = 0; c < N; ++c)
+                lin[c] += pv<R>(2.0 * P.a[c * 4 + cc], P.a2_f[c * 4 + cc]) * r[cc] +
+                          pv<R>(P.kappa[c * 4 + cc], P.kappa_f[c * 4 + cc]) * lp;
         }
-        if constexpr (MU == MU_F64) {
-            double eta = 1.0, rt = 0.0;
+        MT phi[N];
+        if (!mu_node<N, R, FORCE, MU>(r, lin, P, s_tbl, phi)) bad = 1;
 #pragma unroll
-            for (int c = 0; c < N; ++c) {
-                eta -= P.b[c] * r[c];
-                rt += r[c];
-            }
-            ok = ok && eta > 0.0;
-            const double ieta = 1.0 / eta;
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-                double m = P.kT * (log(r[c] * ieta) + P.b[c] * rt * ieta) - lin[c];
-                double ph = P.gamma * m;
-                if constexpr (FORCE == 1) ph -= (1.0 / 3.0) * log(r[c]);
-                s_phi[c][k] = ph;
-            }
-        } else if constexpr (MU == MU_TBL) {
-            const double *t = reinterpret_cast<const double *>(s_tbl);
-            double eta = 1.0, rt = 0.0;
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-                eta = fma(-P.b[c], (double)r[c], eta);
-                rt += (double)r[c];
-            }
-            ok = ok && eta > 0.0;
-            double y = (double)__frcp_rn((float)eta);  // Newton: y <- y + y (1 - eta y), twice
-            y = fma(y, fma(-eta, y, 1.0), y);
-            y = fma(y, fma(-eta, y, 1.0), y);
-            const double rte = rt * y;
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-                double lg = ok ? log64_tbl((double)r[c] * y, t, t + LOG_TBL, t + 2 * LOG_TBL, P.tbl->ln2_hi_d,
-                                           P.tbl->ln2_lo_d)
-                               : 0.0;
-                double ph = fma(P.gkT, fma(P.b[c], rte, lg), -P.gamma * (double)lin[c]);
-                if constexpr (FORCE == 1)
-                    ph -= (1.0 / 3.0) * (ok ? log64_tbl((double)r[c], t, t + LOG_TBL, t + 2 * LOG_TBL,
-                                                         P.tbl->ln2_hi_d, P.tbl->ln2_lo_d)
-                                            : 0.0);
-                s_phi[c][k] = ph;
-            }
-        } else {  // MU_DF
-            df eta = {1.0f, 0.0f}, rt = {0.0f, 0.0f};
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-                eta = df_add(eta, df_neg(df_mul_f({P.b_hi[c], P.b_lo[c]}, r[c])));
-                rt = df_add(rt, {r[c], 0.0f});
-            }
-            ok = ok && eta.hi > 0.0f;
-            const df ieta = df_recip(eta);
-            const df rte = df_mul(rt, ieta);
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-                df lg = ok ? df_log(df_mul_f(ieta, r[c]), s_tbl, s_tbl + LOG_TBL, s_tbl + 2 * LOG_TBL,
-                                    P.tbl->ln2_hi_f, P.tbl->ln2_lo_f)
-                           : df{0.0f, 0.0f};
-                df m = df_add(lg, df_mul(rte, {P.b_hi[c], P.b_lo[c]}));
-                df ph = df_add(df_mul(m, {P.gkT_hi, P.gkT_lo}), df_neg(df_mul_f({P.gamma_hi, P.gamma_lo}, lin[c])));
-                if constexpr (FORCE == 1) {
-                    df lr = ok ? df_log({r[c], 0.0f}, s_tbl, s_tbl + LOG_TBL, s_tbl + 2 * LOG_TBL, P.tbl->ln2_hi_f,
-                                        P.tbl->ln2_lo_f)
-                               : df{0.0f, 0.0f};
-                    ph = df_add(ph, df_neg(df_mul_f(lr, 1.0f / 3.0f)));
-                }
-                s_phi[c][k] = ph;
-            }
-        }
-        if (!ok) bad = 1;
+        for (int c = 0; c < N; ++c) s_phi[c][k] = phi[c];
     }
     __syncthreads();
     if (bad) atomicOr(P.err, ERR_DOMAIN);
@@ -340,117 +517,45 @@ __global__ void __launch_bounds__(TX *TY)
     // ---- phase 3: forces, collision, streaming --------------------------------
     const int ex = tx + 2, ey = ty + 2 * HY;
     const int mx = tx + 1, my = ty + HY;
-
-    R rho[N], ux[N], uy[N], Gx[N], Gy[N], lap[N];
+    R rho[N], lap[N], gpx[N], gpy[N], grx[N], gry[N];
 #pragma unroll
     for (int c = 0; c < N; ++c) {
-        const R rd = s_rho[c][ey * EX + ex];
-        rho[c] = rd;
+        rho[c] = s_rho[c][ey * EX + ex];
         lap[c] = lap_at<LAT, R>(s_rho[c], ex, ey, EX);
-        R gpx, gpy;
-        grad_phi<LAT, R, MT>(s_phi[c], mx, my, MX, gpx, gpy);
-        if constexpr (FORCE == 0) {
-            R grx, gry;
-            grad_at<LAT, R>(s_rho[c], ex, ey, EX, grx, gry);
-            Gx[c] = -rd * gpx + (R)(1.0 / 3.0) * grx;
-            Gy[c] = -rd * gpy + (R)(1.0 / 3.0) * gry;
-        } else {
-            Gx[c] = -rd * gpx;
-            Gy[c] = -rd * gpy;
-        }
-        const R ir = (R)1 / rd;
-        ux[c] = jx[c] * ir;
-        uy[c] = jy[c] * ir;
+        grad_phi<LAT, R, MT>(s_phi[c], mx, my, MX, gpx[c], gpy[c]);
+        if constexpr (FORCE == 0) grad_at<LAT, R>(s_rho[c], ex, ey, EX, grx[c], gry[c]);
+        else grx[c] = gry[c] = (R)0;
     }
-
-    // friction with the implicit u-hat: (D + L/2) h = -L u0, G^f = D h  (per direction)
-    if constexpr (N > 1) {
-        R W[N][N];
+    R gr[N][Q], post[N][Q];
 #pragma unroll
-        for (int c = 0; c < N; ++c)
-#pragma unroll
-            for (int cc = 0; cc < N; ++cc)
-                W[c][cc] = (c == cc) ? (R)0 : (R)P.lam[c * 4 + cc] * rho[c] * rho[cc] / (rho[c] + rho[cc]);
-#pragma unroll
-        for (int d = 0; d < L::D; ++d) {
-            R u0[N], M[N][N], h[N];
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-                R uu = d == 0 ? ux[c] : uy[c];
-                R gg = d == 0 ? Gx[c] : Gy[c];
-                u0[c] = uu + gg / ((R)2 * rho[c]);
-            }
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-                R diag = rho[c], rhs = (R)0;
-#pragma unroll
-                for (int cc = 0; cc < N; ++cc) {
-                    M[c][cc] = (R)(-0.5) * W[c][cc];
-                    diag += (R)0.5 * W[c][cc];
-                    rhs -= W[c][cc] * (u0[c] - u0[cc]);
-                }
-                M[c][c] = diag;
-                h[c] = rhs;
-            }
-            // symmetric positive definite: elimination without pivoting
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-                R inv = (R)1 / M[k][k];
-#pragma unroll
-                for (int r2 = k + 1; r2 < N; ++r2) {
-                    R m = M[r2][k] * inv;
-#pragma unroll
-                    for (int c2 = k + 1; c2 < N; ++c2) M[r2][c2] -= m * M[k][c2];
-                    h[r2] -= m * h[k];
-                }
-            }
-#pragma unroll
-            for (int k = N - 1; k >= 0; --k) {
-                R sacc = h[k];
-#pragma unroll
-                for (int c2 = k + 1; c2 < N; ++c2) sacc -= M[k][c2] * h[c2];
-                h[k] = sacc / M[k][k];
-            }
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-                if (d == 0) Gx[c] += rho[c] * h[c];
-                else Gy[c] += rho[c] * h[c];
-            }
-        }
-    }
-
-    const R omega = (R)P.omega, cg = (R)P.psi_g, cl = (R)P.psi_l;
-#pragma unroll
-    for (int c = 0; c < N; ++c) {
-        const R r = rho[c], u = ux[c], v = uy[c], gx = Gx[c], gy = Gy[c];
-        const R ir = (R)1 / r;
-        // second forcing moment S = G u + u G - Psi, -Psi = cg G G / rho + cl Lap rho I
-        const R Sxx = (R)2 * gx * u + cg * gx * gx * ir + cl * lap[c];
-        const R Syy = (R)2 * gy * v + cg * gy * gy * ir + cl * lap[c];
-        const R Sxy = gx * v + u * gy + cg * gx * gy * ir;
-        const R usq = u * u + v * v;
-        const R drho = r - (R)P.rho_ref[c];
+    for (int c = 0; c < N; ++c)
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            constexpr R third = (R)(1.0 / 3.0);
-            const int cx = L::vx(i), cy = L::vy(i);
-            const R wi = (R)L::w(i);
-            const R vu = (R)cx * u + (R)cy * v;
-            const R vG = (R)cx * gx + (R)cy * gy;
-            // f^eq_i - w_i rho_ref = w_i (rho - rho_ref) + w_i rho (3 v.u + 4.5 (v.u)^2 - 1.5 u^2)
-            const R feq_dev = wi * drho + wi * r * ((R)3 * vu + (R)4.5 * vu * vu - (R)1.5 * usq);
-            R SQ = Sxx * ((R)(cx * cx) - third);
-            if constexpr (LAT == 2) SQ += Syy * ((R)(cy * cy) - third) + (R)2 * Sxy * (R)(cx * cy);
-            const R Fi = wi * ((R)3 * vG + (R)4.5 * SQ);
-            R gi;
-            if constexpr (KEEP) gi = (R)g[c][i];
-            else gi = (R)fin[pop_index(c, i, Q, y, x, nx, ny)];
-            const R post = gi + omega * (feq_dev - gi) + Fi;
-            const int dx = wrap(x + cx, nx);
-            const int dy = (LAT == 1) ? 0 : wrap(y + cy, ny);
-            fout[pop_index(c, i, Q, dy, dx, nx, ny)] = (S)post;
+            if constexpr (KEEP) gr[c][i] = (R)g[c][i];
+            else gr[c][i] = (R)fin[(size_t)(c * Q + i) * plane + (size_t)y * nx + x];
         }
-    }
+    collide_node<LAT, N, R, FORCE>(rho, lap, gpx, gpy, grx, gry, jx, jy, P, gr, post);
+
+    // push streaming to the periodic neighbours
+    const int xe = small ? wrap(x + 1, nx) : (x + 1 == nx ? 0 : x + 1);
+    const int xw = small ? wrap(x - 1, nx) : (x == 0 ? nx - 1 : x - 1);
+    const int yn = LAT == 1 ? 0 : (small ? wrap(y + 1, ny) : (y + 1 == ny ? 0 : y + 1));
+    const int ys = LAT == 1 ? 0 : (small ? wrap(y - 1, ny) : (y == 0 ? ny - 1 : y - 1));
+#pragma unroll
+    for (int c = 0; c < N; ++c)
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int cx = L::vx(i), cy = L::vy(i);
+            const int dx = cx == 1 ? xe : (cx == -1 ? xw : x);
+            const int dy = cy == 1 ? yn : (cy == -1 ? ys : y);
+            fout[(size_t)(c * Q + i) * plane + (size_t)dy * nx + dx] = (S)post[c][i];
+        }
+}
+
+template <int LAT, int N, int TX, int TY, class S, class R, int FORCE, int MU>
+__global__ void __launch_bounds__(TX *TY)
+    lb_step_kernel(const S *__restrict__ fin, S *__restrict__ fout, DevParams P) {
+    step_tile<LAT, N, TX, TY, S, R, FORCE, MU>(fin, fout, P, blockIdx.x * TX, blockIdx.y * TY);
 }
 
 // ---------------------------------------------------------------------------

@@ -3,6 +3,7 @@
 // parallel; lb_api.cu dispatches to them.
 #pragma once
 #include "lb_kernels.cuh"
+#include "lbvdw.h"
 
 namespace lbvdw {
 
@@ -27,6 +28,9 @@ struct FieldLaunch {
     int ncomp;
     cudaStream_t stream;
 };
+
+// parameter block of a parameter set (lb_api.cu); log tables filled on the host
+void make_dev_params(const lb_params &p, DevParams &d, unsigned *err, const LogTables *tbl);
 
 // step launchers: one per lattice and chemical-potential arithmetic
 cudaError_t d1q3_f64_step(const StepLaunch &a);
