@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--tile", default=None, help="D2Q9 tile as TXxTY (default: the library's)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched-sweep measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-rollout measurement")
     ap.add_argument("--only", choices=["fp32_dfmu", "fp32_mixed", "fp64"], default=None,
                     help="time one path only (profiling runs): no e2e, no cpu baseline")
     return ap.parse_args()
@@ -212,6 +213,73 @@ def time_sweep(torch, dev, precision, steps, warmup, dist):
     return out
 
 
+def richardson(fun, x0, h):
+    """Central difference with step h, extrapolated twice (h, h/2, h/4): O(h^6)."""
+    d = [(fun(x0 + s) - fun(x0 - s)) / (2 * s) for s in (h, h / 2, h / 4)]
+    r1 = (4 * d[1] - d[0]) / 3
+    r2 = (4 * d[2] - d[1]) / 3
+    return (16 * r2 - r1) / 15, d[0]
+
+
+def time_adjoint(torch, dev):
+    """Workload c5: D2Q9, 2 components, 512^2, config-2 mixture with a12 = 0.75, 2000 FP64
+    steps checkpointed every 100; loss = sum (rho_T - rho_target)^2 with the target from the
+    FP64 forward at a12 = 0.8.  Times one gradient (forward with checkpoints + backward)
+    and checks it against central finite differences (h = 1e-4, Richardson-extrapolated)."""
+    import numpy as np
+
+    import lbinputs
+    from paper_1805_07251_gb300 import Simulation, capi
+
+    p = lbinputs.base_params("c5")
+    n, steps, ckpt = p["nx"], p["steps"], 100
+    rho0 = lbinputs.fields("c5")
+    st = torch.cuda.current_stream(dev).cuda_stream
+
+    def make(a12, kap):
+        a = p["a"].copy()
+        a[0, 1] = a[1, 0] = a12
+        return Simulation(lattice="D2Q9", nx=n, ny=n, ncomp=2, tau=1.0, kT=p["kT"], gamma_mu=p["gamma_mu"], a=a,
+                          kappa=np.full((2, 2), kap), lam=p["lam"], b=p["b"], precision="fp64", device=dev, stream=st)
+
+    def final(a12, kap, r0):
+        s = make(a12, kap)
+        s.init(r0)
+        s.step(steps)
+        r, _ = s.moments()
+        s.close()
+        return r
+
+    tgt = final(0.8, 0.1, rho0)
+
+    def loss(a12, kap, r0=rho0):
+        return float(np.sum((final(a12, kap, r0) - tgt) ** 2))
+
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    s = make(0.75, 0.1)
+    s.init(rho0)
+    capi.lb_rollout_forward(s.ctx, steps, ckpt)
+    r, _ = s.moments()
+    t1 = time.perf_counter()
+    rb0, g = capi.lb_rollout_backward(s.ctx, 2.0 * (r - tgt), 2)
+    t2 = time.perf_counter()
+    s.close()
+    ga, gk = g[1] + g[2], g[4:8].sum()
+    fa, fa0 = richardson(lambda v: loss(v, 0.1), 0.75, 1e-4)
+    fk, fk0 = richardson(lambda v: loss(0.75, v), 0.1, 1e-4)
+    v = 1e-2 * np.random.default_rng(5).normal(0, 1, rho0.shape)
+    fr, fr0 = richardson(lambda t: loss(0.75, 0.1, rho0 + t * v), 0.0, 1e-4)
+    gr = float(np.sum(rb0 * v))
+    return {"workload": "D2Q9, 2 components, 512x512, a12 = 0.75, 2000 FP64 steps, checkpoint every 100",
+            "s_per_gradient": t2 - t0, "forward_s": t1 - t0, "backward_s": t2 - t1,
+            "grad_a12": ga, "fd_a12": fa, "rel_err_a12": abs(ga - fa) / abs(fa),
+            "grad_kappa": gk, "fd_kappa": fk, "rel_err_kappa": abs(gk - fk) / abs(fk),
+            "grad_rho0_dir": gr, "fd_rho0_dir": fr, "rel_err_rho0_dir": abs(gr - fr) / abs(fr),
+            "fd_plain_h1e-4": {"a12": fa0, "kappa": fk0, "rho0_dir": fr0},
+            "dtype": "f64 (forward and adjoint)"}
+
+
 def time_path(torch, Simulation, kw, rho, precision, steps, warmup, flush, dev):
     """Device time of the fused step kernel: CUDA events on the launching stream around
     each step, L2 flushed before each step outside the events."""
@@ -312,6 +380,9 @@ def main():
     sweep = None
     if not args.only and not args.no_sweep:
         sweep = time_sweep(torch, dev, HEAD, args.steps, args.warmup, dist)
+    adjoint = None
+    if not args.only and not args.no_adjoint and rank == 0:
+        adjoint = time_adjoint(torch, dev)
     e2e = None
     if not args.only:
         # end to end through the C ABI with host buffers: pinned host densities in,
@@ -365,6 +436,8 @@ def main():
     }
     if e2e is not None:
         line["e2e"] = e2e
+    if adjoint is not None:
+        line["adjoint_rollout"] = adjoint
     if sweep is not None:
         if "fp64" in results:
             sweep["vs_fp64_single_run"] = sweep["value"] / results["fp64"]["value"]

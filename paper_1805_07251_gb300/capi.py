@@ -109,6 +109,8 @@ def load():
         "lb_batch_launch_count": (ctypes.c_int64, [C]),
         "lb_batch_last_error": (ctypes.c_char_p, [C]),
         "lb_batch_destroy": (ctypes.c_int, [C]),
+        "lb_rollout_forward": (ctypes.c_int, [C, ctypes.c_int64, ctypes.c_int32]),
+        "lb_rollout_backward": (ctypes.c_int, [C, _DP, _DP, _DP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -289,3 +291,18 @@ def lb_batch_launch_count(b):
 
 def lb_batch_destroy(b):
     load().lb_batch_destroy(b)
+
+
+# --- adjoint rollout ----------------------------------------------------------
+
+def lb_rollout_forward(ctx, nsteps, ckpt_every):
+    _check(ctx, load().lb_rollout_forward(ctx, int(nsteps), int(ckpt_every)), "lb_rollout_forward")
+
+
+def lb_rollout_backward(ctx, rho_bar_T, ncomp):
+    """Returns (rho_bar_0, grad) with grad = [dL/da (N*N), dL/dkappa (N*N), dL/db (N)]."""
+    rho_bar_T = np.ascontiguousarray(rho_bar_T, dtype=np.float64)
+    rb0 = np.empty_like(rho_bar_T)
+    grad = np.empty(2 * ncomp * ncomp + ncomp)
+    _check(ctx, load().lb_rollout_backward(ctx, _dp(rho_bar_T), _dp(rb0), _dp(grad)), "lb_rollout_backward")
+    return rb0, grad

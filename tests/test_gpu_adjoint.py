@@ -1,0 +1,137 @@
+"""GPU tests of the adjoint rollout: the hand-written transpose of the fused FP64 step
+against central finite differences (h = 1e-4) of the GPU forward and of the CPU oracle,
+checkpoint invariance, and the torch.autograd.Function wrapper."""
+import numpy as np
+import pytest
+
+import lbinputs
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def spec_small(lattice, steps):
+    p = lbinputs.base_params("c5")
+    nx, ny = (64, 1) if lattice == "D1Q3" else (24, 20)
+    return dict(lattice=lattice, nx=nx, ny=ny, ncomp=2, tau=1.0, kT=p["kT"], gamma_mu=p["gamma_mu"],
+                a=p["a"], b=p["b"], kappa=0.1, lam=p["lam"], steps=steps)
+
+
+def fields(spec):
+    return lbinputs.fields("c5", nx=spec["nx"], ny=spec["ny"])
+
+
+def target(spec):
+    r = np.random.default_rng(99)
+    return fields(spec) + r.normal(0, 1e-2, (2, spec["ny"], spec["nx"]))
+
+
+def gpu_loss(spec, a12, kappa, b, rho0, tgt):
+    from paper_1805_07251_gb300 import Simulation
+
+    a = np.array(spec["a"], float).copy()
+    a[0, 1] = a[1, 0] = a12
+    sim = Simulation(lattice=spec["lattice"], nx=spec["nx"], ny=spec["ny"], ncomp=2, tau=spec["tau"],
+                     kT=spec["kT"], gamma_mu=spec["gamma_mu"], a=a, kappa=np.full((2, 2), kappa), lam=spec["lam"],
+                     b=b, precision="fp64")
+    sim.init(rho0)
+    sim.step(spec["steps"])
+    r, _ = sim.moments()
+    sim.close()
+    return float(np.sum((r - tgt) ** 2))
+
+
+def oracle_loss(spec, a12, kappa, b, rho0, tgt):
+    a = np.array(spec["a"], float).copy()
+    a[0, 1] = a[1, 0] = a12
+    L = oracle.Lattice(spec["lattice"], spec["nx"], spec["ny"], 2, spec["tau"], spec["kT"], spec["gamma_mu"], a,
+                       np.full((2, 2), kappa), spec["lam"], b)
+    r, _ = L.moments(L.run(L.equilibrium(rho0), spec["steps"]))
+    return float(np.sum((r - tgt) ** 2))
+
+
+def adjoint_grads(spec, rho0, tgt, ckpt):
+    from paper_1805_07251_gb300 import Simulation, capi
+
+    sim = Simulation(lattice=spec["lattice"], nx=spec["nx"], ny=spec["ny"], ncomp=2, tau=spec["tau"],
+                     kT=spec["kT"], gamma_mu=spec["gamma_mu"], a=spec["a"], kappa=np.full((2, 2), spec["kappa"]),
+                     lam=spec["lam"], b=spec["b"], precision="fp64")
+    sim.init(rho0)
+    capi.lb_rollout_forward(sim.ctx, spec["steps"], ckpt)
+    r, _ = sim.moments()
+    rb0, g = capi.lb_rollout_backward(sim.ctx, 2.0 * (r - tgt), 2)
+    sim.close()
+    return rb0, g[0:4].reshape(2, 2), g[4:8].reshape(2, 2), g[8:10]
+
+
+def central(fun, x0, h):
+    """Central difference with step h, Richardson-extrapolated with h/2 so that its own
+    truncation error (O(h^2) through tens of nonlinear steps) stays below the 1e-6 bar."""
+    d1 = (fun(x0 + h) - fun(x0 - h)) / (2 * h)
+    d2 = (fun(x0 + h / 2) - fun(x0 - h / 2)) / h
+    return (4 * d2 - d1) / 3
+
+
+@pytest.mark.parametrize("lattice", ["D1Q3", "D2Q9"])
+def test_adjoint_matches_finite_differences(gpu_lib, lattice):
+    spec = spec_small(lattice, 60)
+    rho0, tgt = fields(spec), target(spec)
+    a12, kap, b = spec["a"][0, 1], spec["kappa"], np.array(spec["b"], float)
+    rb0, ga, gk, gb = adjoint_grads(spec, rho0, tgt, ckpt=25)
+    h = 1e-4
+    fd_a = central(lambda v: gpu_loss(spec, v, kap, b, rho0, tgt), a12, h)
+    assert abs((ga[0, 1] + ga[1, 0]) - fd_a) <= 1e-6 * abs(fd_a)
+    fd_k = central(lambda v: gpu_loss(spec, a12, v, b, rho0, tgt), kap, h)
+    assert abs(gk.sum() - fd_k) <= 1e-6 * abs(fd_k)
+    for c in range(2):
+        e = np.zeros(2); e[c] = 1.0
+        fd_b = central(lambda v: gpu_loss(spec, a12, kap, b + v * e, rho0, tgt), 0.0, h)
+        assert abs(gb[c] - fd_b) <= 1e-6 * abs(fd_b)
+    v = 1e-2 * np.random.default_rng(5).normal(0, 1, rho0.shape)
+    fd_r = central(lambda t: gpu_loss(spec, a12, kap, b, rho0 + t * v, tgt), 0.0, h)
+    assert abs(np.sum(rb0 * v) - fd_r) <= 1e-6 * abs(fd_r)
+
+
+@pytest.mark.parametrize("lattice", ["D1Q3", "D2Q9"])
+def test_adjoint_matches_oracle_finite_differences(gpu_lib, lattice):
+    spec = spec_small(lattice, 40)
+    rho0, tgt = fields(spec), target(spec)
+    a12, kap, b = spec["a"][0, 1], spec["kappa"], np.array(spec["b"], float)
+    rb0, ga, gk, _ = adjoint_grads(spec, rho0, tgt, ckpt=40)
+    h = 1e-4
+    fd_a = central(lambda v: oracle_loss(spec, v, kap, b, rho0, tgt), a12, h)
+    assert abs((ga[0, 1] + ga[1, 0]) - fd_a) <= 1e-6 * abs(fd_a)
+    fd_k = central(lambda v: oracle_loss(spec, a12, v, b, rho0, tgt), kap, h)
+    assert abs(gk.sum() - fd_k) <= 1e-6 * abs(fd_k)
+    v = 1e-2 * np.random.default_rng(6).normal(0, 1, rho0.shape)
+    fd_r = central(lambda t: oracle_loss(spec, a12, kap, b, rho0 + t * v, tgt), 0.0, h)
+    assert abs(np.sum(rb0 * v) - fd_r) <= 1e-6 * abs(fd_r)
+
+
+def test_checkpoint_interval_does_not_change_gradients(gpu_lib):
+    spec = spec_small("D2Q9", 50)
+    rho0, tgt = fields(spec), target(spec)
+    r1 = adjoint_grads(spec, rho0, tgt, ckpt=50)
+    r2 = adjoint_grads(spec, rho0, tgt, ckpt=7)
+    for u, w in zip(r1, r2):
+        assert np.array_equal(u, w)
+
+
+def test_autograd_function(gpu_lib):
+    import torch
+
+    from paper_1805_07251_gb300.adjoint import rollout
+
+    spec = spec_small("D2Q9", 30)
+    spec["ckpt_every"] = 10
+    rho0 = torch.tensor(fields(spec), dtype=torch.float64, requires_grad=True)
+    a12 = torch.tensor(spec["a"][0, 1], dtype=torch.float64, requires_grad=True)
+    kap = torch.tensor(0.1, dtype=torch.float64, requires_grad=True)
+    b = torch.tensor(np.array(spec["b"], float), requires_grad=True)
+    tgt = torch.tensor(target(spec))
+    loss = ((rollout(a12, kap, b, rho0, spec) - tgt) ** 2).sum()
+    loss.backward()
+    rb0, ga, gk, gb = adjoint_grads(spec, fields(spec), target(spec), ckpt=10)
+    assert abs(a12.grad.item() - (ga[0, 1] + ga[1, 0])) <= 1e-12 * abs(a12.grad.item())
+    assert abs(kap.grad.item() - gk.sum()) <= 1e-12 * abs(kap.grad.item())
+    assert np.allclose(rho0.grad.numpy(), rb0, rtol=1e-12, atol=0)

@@ -406,3 +406,31 @@ def test_two_component_slab_lies_on_common_tangent():
     assert len(ph) == 2
     q1, q2 = sorted(ph, key=lambda q: q.sum())
     assert np.max(np.abs(q1 - gas)) < 1e-5 and np.max(np.abs(q2 - liq)) < 1e-5
+
+
+@pytest.mark.parametrize("lam", [0.5, 1.0, 4.0])
+def test_interdiffusion_follows_maxwell_stefan_fick_law(lam):
+    # Sec. IV: with friction lambda between two components, a composition wave at fixed
+    # total density relaxes by Fickian interdiffusion; for two components the
+    # Maxwell-Stefan relation gives -gamma D(mu^A - mu^B) = lambda (u^A - u^B), so
+    # the mode exp(ikx) decays at rate gamma rho^A rho^B h k^2 / (rho lambda), with
+    # h = H_AA - H_AB - H_BA + H_BB the bulk Hessian along the composition direction.
+    a = np.array([[1.0, 0.7], [0.7, 1.0]]); b = np.array([0.25, 0.25])
+    kT = 1.2 * T.one_fluid_critical_temperature(a, b, [0.5, 0.5])
+    nx, gam, rA, rho, eps = 128, 0.5, 0.5, 1.0, 1e-4
+    x = np.arange(nx)
+    k = 2 * np.pi / nx
+    H = T.hessian(kT, a, b, np.array([rA, rho - rA]))
+    h = H[0, 0] - H[0, 1] - H[1, 0] + H[1, 1]
+    L = lat("D1Q3", nx, 1, 2, kT=kT, gamma=gam, a=a, b=b, kappa=0.1, lam=[[0, lam], [lam, 0]])
+    r0 = np.stack([rA + eps * np.cos(k * x), rho - rA - eps * np.cos(k * x)]).reshape(L.rshape())
+    f = L.equilibrium(r0)
+    ts, amps = [], []
+    for t in range(1, 41):
+        f = L.run(f, 200)
+        r, _ = L.moments(f)
+        ts.append(200 * t)
+        amps.append(np.abs(np.mean(0.5 * (r[0, 0] - r[1, 0]) * np.exp(-1j * k * x))))
+    rate = -np.polyfit(ts[15:], np.log(amps[15:]), 1)[0]
+    predicted = gam * rA * (rho - rA) * h * k * k / (rho * lam)
+    assert abs(rate / predicted - 1) < 0.01

@@ -157,3 +157,32 @@ def test_two_phase_tie_line_lever_rule_and_stability():
     f = T.free_energy_density(kT, a, b, g)
     plane = T.free_energy_density(kT, a, b, r1) + mu1 @ (g - r1[:, None])
     assert np.min(f - plane) > -1e-9
+
+
+def test_appendix_a_minimiser_agrees_with_convex_hull():
+    # Appendix A's quasi-brute-force three-phase minimiser and the convex-hull common
+    # tangent (two independent minimisations of the same bulk free energy) agree on the
+    # baseline three-phase point (Sec. VI, paper: minimiser uncertainty ~1e-6), on a
+    # two-phase point, and on a stable mean (one phase).
+    from oracle import appendix_a as AA
+
+    a, b, _ = T.mixture_from_critical(0.4, 0.4, 1.0, 0.5, 0.1)
+    hull = sorted(T.coexistence(1 / 3, a, b, [0.8, 0.8], n=400), key=lambda q: (q.sum(), q[0]))
+    mini = AA.minimise(1 / 3, a, b, [0.8, 0.8])
+    assert len(mini) == 3
+    got = sorted([r for r, _ in mini], key=lambda q: (q.sum(), q[0]))
+    for g, h in zip(got, hull):
+        assert np.max(np.abs(g - h)) < 1e-5
+    assert abs(sum(v for _, v in mini) - 1.0) < 1e-12
+    a2 = np.array([[1.0, 0.9], [0.9, 0.6]]); b2 = np.array([0.25, 0.3])
+    kT = 0.85 * T.one_fluid_critical_temperature(a2, b2, [0.4, 0.6])
+    mean = 1.2 * np.array([0.4, 0.6])
+    mini = AA.minimise(kT, a2, b2, mean)
+    hull = sorted(T.coexistence(kT, a2, b2, mean, n=400), key=lambda q: q.sum())
+    assert len(mini) == 2
+    for (g, _), h in zip(mini, hull):
+        assert np.max(np.abs(g - h)) < 1e-5
+    # lever rule: volume-weighted densities give back the mean
+    assert np.max(np.abs(sum(v * r for r, v in mini) - mean)) < 1e-9
+    one = AA.minimise(kT, a2, b2, [0.02, 0.02])
+    assert len(one) == 1
