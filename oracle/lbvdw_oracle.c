@@ -353,8 +353,16 @@ static int step(const orc_params *p, const lattice_t *L, double *f, work_t *w) {
                 double usq = u[0] * u[0] + u[1] * u[1];
                 /* stage 6: Hermite equilibrium (Eq. feq) and forcing populations
                  * F_i = w_i [ v.G/theta + S:(v v - theta I)/(2 theta^2) ], whose
-                 * moments are 0, G and S (Sec. III) */
-                for (int i = 0; i < Q; ++i) {
+                 * moments are 0, G and S (Sec. III).  The moving populations
+                 * (i = 1 .. Q-1) come from these forms; the rest population (i = 0)
+                 * from the zeroth-moment conditions that define f^eq and F in
+                 * Sec. III, sum_i f_i^eq = rho and sum_i F_i = 0 (the Hermite forms
+                 * satisfy them in exact arithmetic, but the rounded weights w_i do not
+                 * sum to one, which would change the mass by a fixed fraction each
+                 * step). */
+                double feq_moving = 0.0, F_moving = 0.0;
+                for (int k = 1; k <= Q; ++k) {
+                    const int i = k % Q; /* 1, 2, ..., Q-1, then the rest population 0 */
                     double v[2] = {(double)L->vx[i], (double)L->vy[i]};
                     double vu = v[0] * u[0] + v[1] * u[1];
                     double feq = r * L->w[i] *
@@ -366,6 +374,13 @@ static int step(const orc_params *p, const lattice_t *L, double *f, work_t *w) {
                         for (int bb = 0; bb < D; ++bb)
                             SQ += S[a][bb] * (v[a] * v[bb] - (a == bb ? THETA : 0.0));
                     double Fi = L->w[i] * (vG / THETA + SQ / (2.0 * THETA * THETA));
+                    if (i == 0) {
+                        feq = r - feq_moving;
+                        Fi = -F_moving;
+                    } else {
+                        feq_moving += feq;
+                        F_moving += Fi;
+                    }
                     double fi = f[((long)c * Q + i) * n + s];
                     /* BGK (Eq. BGKcollisionOperator, single relaxation time) */
                     double post = fi + (feq - fi) / p->tau + Fi;

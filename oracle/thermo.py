@@ -165,12 +165,24 @@ def maxwell_1c(kT, a, b, tol=1e-14, maxit=200):
     def dmu(r):
         return float(hessian(kT, A, B, np.array([r]))[0, 0])
 
-    # start: bracket by p at the spinodal mid pressure
-    pm = 0.5 * (p(sp[0]) + p(sp[1]))
+    # start: for a pressure P between the spinodal pressures (and above 0) take the gas
+    # and liquid densities with p = P; the coexistence pressure is the root of
+    # mu_gas(P) - mu_liquid(P) (equal-area rule), found by bisection, then Newton
     from scipy.optimize import brentq
-    rg = brentq(lambda r: p(r) - pm, 1e-12, sp[0])
-    rl = brentq(lambda r: p(r) - pm, sp[1], (1.0 - 1e-12) / b)
-    x = np.array([rg, rl])
+    p_lo = max(p(sp[1]), 1e-300)
+    p_hi = p(sp[0])
+
+    def branch(P):
+        rg = brentq(lambda r: p(r) - P, 1e-300, sp[0], xtol=1e-300, rtol=1e-15, maxiter=500)
+        rl = brentq(lambda r: p(r) - P, sp[1], (1.0 - 1e-15) / b, xtol=1e-300, rtol=1e-15, maxiter=500)
+        return rg, rl
+
+    def dmu_of(P):
+        rg, rl = branch(P)
+        return mu(rg) - mu(rl)
+
+    P = brentq(dmu_of, p_lo * (1 + 1e-12), p_hi * (1 - 1e-12), rtol=1e-14, maxiter=500)
+    x = np.array(branch(P))
     for _ in range(maxit):
         F = np.array([mu(x[0]) - mu(x[1]), p(x[0]) - p(x[1])])
         # dp/drho = rho dmu/drho
@@ -324,6 +336,49 @@ def polish_three_phase(kT, a, b, ph1, ph2, ph3, tol=1e-13, maxit=100):
             break
     return x[0:2].copy(), x[2:4].copy(), x[4:6].copy()
 
+
+
+def polish_invariant_point(kT, a, b, phases, tol=1e-14, maxit=100):
+    """Newton solve for N + 1 coexisting phases of an N-component mixture (Sec. II: equal
+    chemical potentials mu^c and equal pressure in every phase; with N + 1 phases at fixed
+    kT the Gibbs phase rule leaves no freedom, so the point is isolated).  ``phases`` is a
+    list of N + 1 starting density vectors; returns the polished list.  The Jacobian is
+    analytic: d mu / d rho is the Hessian H of the free-energy density and
+    d p / d rho = rho^T H (from dp = sum_c rho^c d mu^c)."""
+    a = np.asarray(a, float)
+    b = np.asarray(b, float)
+    P = len(phases)
+    N = len(b)
+    if P != N + 1:
+        raise ValueError("an invariant point has N + 1 phases")
+    x = np.concatenate([np.asarray(q, float) for q in phases])
+    for _ in range(maxit):
+        r = [x[q * N:(q + 1) * N] for q in range(P)]
+        mu = [chemical_potential(kT, a, b, ri) for ri in r]
+        p = [pressure(kT, a, b, ri) for ri in r]
+        H = [hessian(kT, a, b, ri) for ri in r]
+        F = np.zeros((P - 1) * (N + 1))
+        J = np.zeros(((P - 1) * (N + 1), P * N))
+        for q in range(1, P):
+            row = (q - 1) * (N + 1)
+            F[row:row + N] = mu[q] - mu[0]
+            F[row + N] = p[q] - p[0]
+            J[row:row + N, q * N:(q + 1) * N] = H[q]
+            J[row:row + N, 0:N] = -H[0]
+            J[row + N, q * N:(q + 1) * N] = r[q] @ H[q]
+            J[row + N, 0:N] = -(r[0] @ H[0])
+        dx = np.linalg.solve(J, -F)
+        lam = 1.0
+        while True:
+            xn = x + lam * dx
+            ok = np.all(xn > 0) and all(b @ xn[q * N:(q + 1) * N] < 1 for q in range(P))
+            if ok or lam < 1e-6:
+                break
+            lam *= 0.5
+        x = xn
+        if np.max(np.abs(lam * dx) / np.maximum(np.abs(x), 1e-300)) < tol:
+            break
+    return [x[q * N:(q + 1) * N].copy() for q in range(P)]
 
 def coexistence(kT, a, b, rho_mean, hull=None, n=600):
     """Coexisting phases for a two-component mean state: a list of 1, 2 or 3

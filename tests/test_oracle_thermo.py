@@ -186,3 +186,35 @@ def test_appendix_a_minimiser_agrees_with_convex_hull():
     assert np.max(np.abs(sum(v * r for r, v in mini) - mean)) < 1e-9
     one = AA.minimise(kT, a2, b2, [0.02, 0.02])
     assert len(one) == 1
+
+
+def test_invariant_point_solver():
+    # N + 1 coexisting phases (Sec. II conditions).  Two components: the baseline
+    # three-phase triangle of the convex hull (an independent minimisation) is
+    # reproduced.  Three components (Sec. VI, Fig. graphLB3Components: theta_cr = 0.5,
+    # rho_cr = 1, nu = 0.05, theta = 1/3): a four-phase point whose common tangent
+    # hyperplane lies below the free energy everywhere on a grid of the domain.
+    a, b, _ = T.mixture_from_critical(0.4, 0.4, 1.0, 0.5, 0.1)
+    hull = sorted(T.coexistence(1 / 3, a, b, [0.8, 0.8], n=400), key=lambda q: (q.sum(), q[0]))
+    start = [q + 1e-3 for q in hull]
+    inv = sorted(T.polish_invariant_point(1 / 3, a, b, start), key=lambda q: (q.sum(), q[0]))
+    for g, h in zip(inv, hull):
+        assert np.max(np.abs(g - h)) < 1e-10
+    aa, bb = T.ab_from_critical(0.5, 1.0)
+    a3 = np.full((3, 3), 0.05 * aa)
+    np.fill_diagonal(a3, aa)
+    b3 = np.full(3, bb)
+    guess = [np.array([2.2, 1e-3, 1e-3]), np.array([1e-3, 2.2, 1e-3]), np.array([1e-3, 1e-3, 2.2]),
+             np.array([0.1, 0.1, 0.1])]
+    ph = T.polish_invariant_point(1 / 3, a3, b3, guess)
+    mu = T.chemical_potential(1 / 3, a3, b3, ph[0])
+    for q in ph:
+        assert not T.is_unstable(1 / 3, a3, b3, q)
+    # symmetric under permutations of the components
+    assert np.max(np.abs(ph[1] - ph[0][[1, 0, 2]])) < 1e-12 and np.max(np.abs(ph[2] - ph[0][[2, 1, 0]])) < 1e-12
+    g = np.linspace(1e-4, 2.95, 48)
+    G = np.stack(np.meshgrid(g, g, g, indexing="ij")).reshape(3, -1)
+    G = G[:, b3 @ G < 0.999]
+    f = T.free_energy_density(1 / 3, a3, b3, G)
+    plane = T.free_energy_density(1 / 3, a3, b3, ph[0]) + mu @ (G - ph[0][:, None])
+    assert np.min(f - plane) > -1e-12
