@@ -53,8 +53,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--tile", default=None, help="D2Q9 tile as TXxTY (default: the library's)")
+    ap.add_argument("--kernel", choices=["auto", "tiles", "strips"], default="auto",
+                    help="organisation of the step kernel (default: the library's choice)")
+    ap.add_argument("--segments", type=int, default=0, help="strips: row segments per strip (0 = library's)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched-sweep measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-rollout measurement")
+    ap.add_argument("--no-c4", action="store_true", help="skip the four-component measurement")
     ap.add_argument("--only", choices=["fp32_dfmu", "fp32_mixed", "fp64"], default=None,
                     help="time one path only (profiling runs): no e2e, no cpu baseline")
     return ap.parse_args()
@@ -213,6 +217,50 @@ def time_sweep(torch, dev, precision, steps, warmup, dist):
     return out
 
 
+def time_c4(torch, dev, precision, steps, warmup):
+    """Workload c4: D2Q9, 4 components, 2048 x 2048 (604 MB of FP32 populations per
+    buffer, larger than the L2), seeded random symmetric mixture, kT = 0.8 of the
+    one-fluid critical temperature.  Times `steps` timesteps, then runs on to the
+    configuration's 5000 steps and reports the per-component mass drift."""
+    import numpy as np
+
+    import lbinputs
+    from paper_1805_07251_gb300 import Simulation
+
+    p = lbinputs.base_params("c4")
+    kw = lbinputs.lib_kwargs(p)
+    rho = lbinputs.fields("c4")
+    m0 = rho.reshape(p["ncomp"], -1).sum(axis=1)
+    stream = torch.cuda.current_stream(dev)
+    sim = Simulation(precision=precision, device=dev, stream=stream.cuda_stream, **kw)
+    sim.init(rho)
+    sim.step(warmup)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = sim.launches
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    launches = sim.launches - l0
+    sim.step(p["steps"] - steps - warmup)
+    status = "ok"
+    try:
+        _, mass, _ = sim.free_energy()
+        drift = float(np.max(np.abs(mass - m0) / m0))
+    except Exception as e:  # a domain error is reported, not raised
+        drift, status = None, str(e)
+    sim.close()
+    nodes = p["nx"] * p["ny"]
+    N = p["ncomp"]
+    return {"workload": "D2Q9, 4 components, 2048x2048, seeded mixture, kT = 0.8 theta_cr^mix",
+            "value": N * nodes / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+            "roofline_hbm": {"achieved": N * nodes * 9 * 2 * 4 / (ms * 1e-3) / 1e9},
+            "steps_total": p["steps"], "mass_drift_max_rel": drift, "status": status,
+            "dtype": DTYPES[precision], "gpu_launches": launches, "l2": "state larger than L2, no flush"}
+
+
 def richardson(fun, x0, h):
     """Central difference with step h, extrapolated twice (h, h/2, h/4): O(h^6)."""
     d = [(fun(x0 + s) - fun(x0 - s)) / (2 * s) for s in (h, h / 2, h / 4)]
@@ -222,10 +270,11 @@ def richardson(fun, x0, h):
 
 
 def time_adjoint(torch, dev):
-    """Workload c5: D2Q9, 2 components, 512^2, config-2 mixture with a12 = 0.75, 2000 FP64
-    steps checkpointed every 100; loss = sum (rho_T - rho_target)^2 with the target from the
-    FP64 forward at a12 = 0.8.  Times one gradient (forward with checkpoints + backward)
-    and checks it against central finite differences (h = 1e-4, Richardson-extrapolated)."""
+    """Workload c5: D2Q9, 2 components, 512^2, config-2 mixture and temperature with
+    a12 = 0.75, 2000 FP64 steps checkpointed every 100; loss = sum (rho_T - rho_target)^2
+    with the target from the FP64 forward at a12 = 0.8.  Times one gradient (forward with
+    checkpoints + backward) and checks it against central finite differences (h = 1e-4,
+    Richardson-extrapolated)."""
     import numpy as np
 
     import lbinputs
@@ -271,7 +320,8 @@ def time_adjoint(torch, dev):
     v = 1e-2 * np.random.default_rng(5).normal(0, 1, rho0.shape)
     fr, fr0 = richardson(lambda t: loss(0.75, 0.1, rho0 + t * v), 0.0, 1e-4)
     gr = float(np.sum(rb0 * v))
-    return {"workload": "D2Q9, 2 components, 512x512, a12 = 0.75, 2000 FP64 steps, checkpoint every 100",
+    return {"workload": "D2Q9, 2 components, %dx%d, a12 = 0.75, gamma_mu = %.4g, %d FP64 steps, checkpoint every %d"
+                        % (n, n, p["gamma_mu"], steps, ckpt),
             "s_per_gradient": t2 - t0, "forward_s": t1 - t0, "backward_s": t2 - t1,
             "grad_a12": ga, "fd_a12": fa, "rel_err_a12": abs(ga - fa) / abs(fa),
             "grad_kappa": gk, "fd_kappa": fk, "rel_err_kappa": abs(gk - fk) / abs(fk),
@@ -284,7 +334,8 @@ def time_path(torch, Simulation, kw, rho, precision, steps, warmup, flush, dev):
     """Device time of the fused step kernel: CUDA events on the launching stream around
     each step, L2 flushed before each step outside the events."""
     stream = torch.cuda.current_stream(dev)
-    sim = Simulation(precision=precision, device=dev, stream=stream.cuda_stream, tile=TILE, **kw)
+    sim = Simulation(precision=precision, device=dev, stream=stream.cuda_stream, tile=TILE,
+                     kernel=KERNEL if precision != "fp64" else "auto", segments=SEGMENTS, **kw)
     sim.init(rho)
     for _ in range(warmup):
         flush.zero_()
@@ -296,13 +347,16 @@ def time_path(torch, Simulation, kw, rho, precision, steps, warmup, flush, dev):
 
 
 TILE = None
+KERNEL = "auto"
+SEGMENTS = 0
 
 
 def main():
-    global TILE
+    global TILE, KERNEL, SEGMENTS
     args = parse()
     if args.tile:
         TILE = tuple(int(v) for v in args.tile.lower().split("x"))
+    KERNEL, SEGMENTS = args.kernel, args.segments
     if args.impl == "reference":
         return run_reference(args)
     if args.warmup < 3:
@@ -369,20 +423,30 @@ def main():
             t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             total_ms = float(t.item())
+        kind, tile = sim.kernel
         ms = total_ms / args.steps
         value = world * N * nodes * args.steps / (total_ms * 1e-3) / 1e6
         elem = 8 if precision == "fp64" else 4
         alg_bytes = N * nodes * 9 * 2 * elem
         achieved = alg_bytes / (ms * 1e-3) / 1e9
-        results[precision] = dict(value=value, ms=ms, launches=launches, alg_bytes=alg_bytes, achieved=achieved)
+        results[precision] = dict(value=value, ms=ms, launches=launches, alg_bytes=alg_bytes, achieved=achieved,
+                                  kernel="%s %dx%d" % (kind, tile[0], tile[1]))
         sim.close()
 
     sweep = None
     if not args.only and not args.no_sweep:
         sweep = time_sweep(torch, dev, HEAD, args.steps, args.warmup, dist)
+    c4 = None
+    if not args.only and not args.no_c4:
+        c4 = time_c4(torch, dev, HEAD, args.steps, args.warmup)
     adjoint = None
     if not args.only and not args.no_adjoint and rank == 0:
-        adjoint = time_adjoint(torch, dev)
+        from paper_1805_07251_gb300 import capi as _capi
+
+        try:
+            adjoint = time_adjoint(torch, dev)
+        except _capi.LBError as e:  # a run of the gradient check left the domain
+            adjoint = {"error": str(e)}
     e2e = None
     if not args.only:
         # end to end through the C ABI with host buffers: pinned host densities in,
@@ -426,11 +490,13 @@ def main():
         "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPES[HEAD], "data": "synthetic",
         "config": {"workload": "D2Q9, 2 components, 1024x1024 periodic, spinodal mixture (c2), " + HEAD,
-                   "nodes": nodes, "ncomp": N, "tile": args.tile or "32x8", "l2": "flushed between steps (256 MB write)",
+                   "nodes": nodes, "ncomp": N, "kernel": head["kernel"], "l2": "flushed between steps (256 MB write)",
                    "parallelism": "independent replica per GPU" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": head["achieved"], "peak": peak_gbs, "unit": "GB/s",
                      "frac": head["achieved"] / peak_gbs, "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "lb_step_kernel<D2Q9, N=2, 32x8, %s>" % HEAD,
+                     "kernel": "%s<D2Q9, N=2, %s, %s>" % (
+                         "lb_strip_kernel" if head["kernel"].startswith("strips") else "lb_step_kernel",
+                         head["kernel"].split()[1], HEAD),
                      "alg_bytes_per_launch": head["alg_bytes"]},
         "gpu_launches": head["launches"],
     }
@@ -438,6 +504,10 @@ def main():
         line["e2e"] = e2e
     if adjoint is not None:
         line["adjoint_rollout"] = adjoint
+    if c4 is not None:
+        c4["roofline_hbm"].update({"peak": peak_gbs, "unit": "GB/s", "frac": c4["roofline_hbm"]["achieved"] / peak_gbs})
+        line["four_components"] = c4
+        line["gpu_launches"] += c4["gpu_launches"]
     if sweep is not None:
         if "fp64" in results:
             sweep["vs_fp64_single_run"] = sweep["value"] / results["fp64"]["value"]
@@ -448,6 +518,7 @@ def main():
             continue
         rr = results[key]
         line[name] = {"value": rr["value"], "unit": UNIT, "ms_per_step": rr["ms"], "dtype": DTYPES[key],
+                      "kernel": rr["kernel"],
                       "roofline_hbm": {"achieved": rr["achieved"], "peak": peak_gbs, "unit": "GB/s",
                                        "frac": rr["achieved"] / peak_gbs}}
         line["gpu_launches"] += rr["launches"]

@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define LBVDW_ABI 1
+#define LBVDW_ABI 2
 
 typedef enum {
     LB_OK = 0,
@@ -80,6 +80,22 @@ typedef enum {
 
 typedef enum { LB_FORCE_LOG = 0, LB_FORCE_NID = 1 } lb_force_method;
 
+/* Organisation of the fused step kernel (the arithmetic, and so every result, is
+ * the same bit for bit):
+ *   LB_KERNEL_TILES   one CTA per tile_x x tile_y tile; each tile recomputes rho on a
+ *                     2-node ring and mu on a 1-node ring around itself.
+ *   LB_KERNEL_STRIPS  (D2Q9, FP32 storage) one CTA per column strip tile_x nodes wide
+ *                     and per segment of its rows, walking down the segment tile_y
+ *                     rows at a time; the populations of the rows ahead arrive in
+ *                     shared memory by asynchronous bulk copies (cp.async.bulk with
+ *                     mbarrier completion) while the current rows are collided.
+ *                     Needs nx % tile_x == 0 and ny % tile_y == 0, with
+ *                     (tile_x, tile_y) = (32, 8) for 1-2 components, (32, 4) for 3-4.
+ *   LB_KERNEL_AUTO    tiles (measured faster on GB300: 34.7k against 25.2k component-
+ *                     MLUPS for 2 components at 1024^2; the strips' shared-memory
+ *                     staging leaves two CTAs, 18 warps, per SM). */
+typedef enum { LB_KERNEL_AUTO = 0, LB_KERNEL_TILES = 1, LB_KERNEL_STRIPS = 2 } lb_kernel_kind;
+
 typedef struct {
     uint32_t abi;        /* must equal LBVDW_ABI */
     int32_t lattice;     /* lb_lattice */
@@ -101,8 +117,11 @@ typedef struct {
                             rest equilibrium is subtracted before FP32 storage; 0 = use
                             the mean density set by lb_init_fields */
     int32_t device;      /* CUDA device ordinal */
-    int32_t tile_x, tile_y; /* 0 = default; D2Q9: 32x8, 64x4, 32x16 or 64x8;
-                               D1Q3: 128x1 or 256x1 */
+    int32_t tile_x, tile_y; /* 0 = default; tiles: D2Q9 32x8, 64x4, 32x16 or 64x8,
+                               D1Q3 128x1 or 256x1; strips: see lb_kernel_kind */
+    int32_t kernel;      /* lb_kernel_kind */
+    int32_t segments;    /* strips: row segments per strip (0 = enough CTAs to fill the
+                            GPU once); ignored by tiles */
     void *stream;        /* cudaStream_t for every launch and copy; NULL = legacy default */
 } lb_params;
 
@@ -263,6 +282,11 @@ int64_t lb_step_count(const lb_ctx *ctx);
 
 /* Kernel launches enqueued by this context since creation (for launch accounting). */
 int64_t lb_launch_count(const lb_ctx *ctx);
+
+/* Copy the context's parameters as resolved by lb_create (kernel organisation and
+ * tile chosen for LB_KERNEL_AUTO and tile 0 x 0) into *out.  Errors: LB_E_INVALID
+ * (NULL argument). */
+lb_status lb_get_params(const lb_ctx *ctx, lb_params *out);
 
 /* Release every device buffer of the context and the context itself (NULL is a no-op). */
 lb_status lb_destroy(lb_ctx *ctx);

@@ -16,11 +16,12 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "liblbvdw.so")
 
-LBVDW_ABI = 1
+LBVDW_ABI = 2
 LB_OK, LB_E_INVALID, LB_E_NOMEM, LB_E_CUDA, LB_E_DOMAIN, LB_E_TIMEOUT, LB_E_STATE = range(7)
 LB_D1Q3, LB_D2Q9 = 1, 2
 LB_FP64, LB_FP32_MIXED, LB_FP32_DFMU = 0, 1, 2
 LB_FORCE_LOG, LB_FORCE_NID = 0, 1
+LB_KERNEL_AUTO, LB_KERNEL_TILES, LB_KERNEL_STRIPS = 0, 1, 2
 
 
 class lb_run_desc(ctypes.Structure):
@@ -54,6 +55,8 @@ class lb_params(ctypes.Structure):
         ("device", ctypes.c_int32),
         ("tile_x", ctypes.c_int32),
         ("tile_y", ctypes.c_int32),
+        ("kernel", ctypes.c_int32),
+        ("segments", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -93,6 +96,7 @@ def load():
         "lb_load_state": (ctypes.c_int, [C, C, ctypes.c_size_t]),
         "lb_step_count": (ctypes.c_int64, [C]),
         "lb_launch_count": (ctypes.c_int64, [C]),
+        "lb_get_params": (ctypes.c_int, [C, ctypes.POINTER(lb_params)]),
         "lb_destroy": (ctypes.c_int, [C]),
         "lb_status_str": (ctypes.c_char_p, [ctypes.c_int]),
         "lb_last_error": (ctypes.c_char_p, [C]),
@@ -205,6 +209,12 @@ def lb_step_count(ctx):
 
 def lb_launch_count(ctx):
     return int(load().lb_launch_count(ctx))
+
+
+def lb_get_params(ctx):
+    p = lb_params()
+    _check(ctx, load().lb_get_params(ctx, ctypes.byref(p)), "lb_get_params")
+    return p
 
 
 def lb_destroy(ctx):

@@ -59,8 +59,11 @@ cudaError_t run_step(lb_ctx *c) {
     a.force = c->p.force_method;
     a.tile_x = c->p.tile_x;
     a.tile_y = c->p.tile_y;
+    a.kernel = c->p.kernel;
+    a.segs = c->p.segments;
     a.stream = c->stream;
     const bool d1 = c->p.lattice == LB_D1Q3;
+    if (a.kernel == LB_KERNEL_STRIPS) return c->p.precision == LB_FP32_MIXED ? d2q9_tbl_strip(a) : d2q9_df_strip(a);
     switch (c->p.precision) {
         case LB_FP32_MIXED: return d1 ? d1q3_tbl_step(a) : d2q9_tbl_step(a);
         case LB_FP32_DFMU: return d1 ? d1q3_df_step(a) : d2q9_df_step(a);
@@ -99,6 +102,7 @@ lb_status sync_check(lb_ctx *c) {
     unsigned h = 0;
     LB_CUDA(c, cudaMemcpyAsync(&h, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (h & ERR_TIMEOUT) return fail(c, LB_E_TIMEOUT, "a step kernel's wait for its bulk copies ran out");
     if (h & ERR_DOMAIN) return fail(c, LB_E_DOMAIN, "a density or eta <= 0, or a non-finite value, was met");
     return LB_OK;
 }
@@ -255,18 +259,35 @@ lb_status lb_create(const lb_params *p, lb_ctx **out) {
             if (cc != c && p->lambda[c * 4 + cc] < 0.0) return LB_E_INVALID;
     }
     if (p->check_every < 0) return LB_E_INVALID;
+    if (p->kernel < LB_KERNEL_AUTO || p->kernel > LB_KERNEL_STRIPS || p->segments < 0) return LB_E_INVALID;
 
     lb_ctx *c = new (std::nothrow) lb_ctx;
     if (!c) return LB_E_NOMEM;
     c->p = *p;
-    if (c->p.tile_x == 0 && c->p.tile_y == 0) {
-        c->p.tile_x = p->lattice == LB_D1Q3 ? 128 : 32;
-        c->p.tile_y = p->lattice == LB_D1Q3 ? 1 : 8;
+    // kernel organisation: AUTO takes tiles, the faster organisation on GB300 for every
+    // measured workload (strips hold two CTAs per SM, too few warps to hide latency)
+    const bool no_tile = p->tile_x == 0 && p->tile_y == 0;
+    const bool strips_ok = p->lattice == LB_D2Q9 && p->precision != LB_FP64 && strip_shape_ok(p->nx, p->ny, N);
+    int kind = p->kernel;
+    if (kind == LB_KERNEL_AUTO) kind = LB_KERNEL_TILES;
+    c->p.kernel = kind;
+    bool tile_ok;
+    if (kind == LB_KERNEL_STRIPS) {
+        if (no_tile) {
+            c->p.tile_x = STRIP_TX;
+            c->p.tile_y = strip_ty(N);
+        }
+        tile_ok = strips_ok && c->p.tile_x == STRIP_TX && c->p.tile_y == strip_ty(N);
+    } else {
+        if (no_tile) {
+            c->p.tile_x = p->lattice == LB_D1Q3 ? 128 : 32;
+            c->p.tile_y = p->lattice == LB_D1Q3 ? 1 : 8;
+        }
+        tile_ok = p->lattice == LB_D1Q3
+                      ? (c->p.tile_y == 1 && (c->p.tile_x == 128 || c->p.tile_x == 256))
+                      : ((c->p.tile_x == 32 && c->p.tile_y == 8) || (c->p.tile_x == 64 && c->p.tile_y == 4) ||
+                         (c->p.tile_x == 32 && c->p.tile_y == 16) || (c->p.tile_x == 64 && c->p.tile_y == 8));
     }
-    bool tile_ok = p->lattice == LB_D1Q3
-                       ? (c->p.tile_y == 1 && (c->p.tile_x == 128 || c->p.tile_x == 256))
-                       : ((c->p.tile_x == 32 && c->p.tile_y == 8) || (c->p.tile_x == 64 && c->p.tile_y == 4) ||
-                          (c->p.tile_x == 32 && c->p.tile_y == 16) || (c->p.tile_x == 64 && c->p.tile_y == 8));
     if (!tile_ok) { delete c; return LB_E_INVALID; }
     c->Q = p->lattice == LB_D1Q3 ? 3 : 9;
     c->D = p->lattice == LB_D1Q3 ? 1 : 2;
@@ -511,6 +532,12 @@ lb_status lb_load_state(lb_ctx *c, const void *buf, size_t bytes) {
 int64_t lb_step_count(const lb_ctx *c) { return c ? c->steps : -1; }
 
 int64_t lb_launch_count(const lb_ctx *c) { return c ? c->launches : -1; }
+
+lb_status lb_get_params(const lb_ctx *c, lb_params *out) {
+    if (!c || !out) return LB_E_INVALID;
+    *out = c->p;
+    return LB_OK;
+}
 
 lb_status lb_destroy(lb_ctx *c) {
     if (!c) return LB_OK;

@@ -4,4 +4,5 @@
 #define LBVDW_R float
 #define LBVDW_MU MU_DF
 #define LBVDW_NAME d2q9_df
+#define LBVDW_STRIPS 1
 #include "lb_tu.cuh"

@@ -5,4 +5,5 @@
 #define LBVDW_MU MU_TBL
 #define LBVDW_NAME d2q9_tbl
 #define LBVDW_FIELDS d2q9_f32
+#define LBVDW_STRIPS 1
 #include "lb_tu.cuh"

@@ -23,6 +23,7 @@
 namespace lbvdw {
 
 constexpr unsigned ERR_DOMAIN = 1u;   // rho^c <= 0, eta <= 0 or non-finite value
+constexpr unsigned ERR_TIMEOUT = 2u;  // a bounded wait for bulk copies ran out (lb_strip.cuh)
 
 struct DevParams {
     int nx, ny;
@@ -138,11 +139,15 @@ template <> struct MuStore<MU_F64> { using T = double; };
 template <> struct MuStore<MU_TBL> { using T = double; };
 template <> struct MuStore<MU_DF> { using T = df; };
 
-// phi difference a - b in the mu arithmetic, rounded to R
+// phi difference a - b in the mu arithmetic, rounded to R.  For df values the high
+// parts are subtracted first: exact when they are within a factor 2 (Sterbenz), else
+// rounded once at the precision of the result, which is rounded to FP32 anyway.
 template <class R>
 __device__ __forceinline__ R phi_diff(double a, double b) { return (R)(a - b); }
 template <class R>
-__device__ __forceinline__ R phi_diff(df a, df b) { return (R)df_to_float(df_add(a, df_neg(b))); }
+__device__ __forceinline__ R phi_diff(df a, df b) {
+    return (R)__fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
+}
 
 // D phi at (mx, my) of an MX-wide shared array, differences in the mu arithmetic
 template <int LAT, class R, class T>
@@ -362,15 +367,12 @@ __device__ __forceinline__ void collide_node(const R (&rho)[N], const R (&lap)[N
         // Directions come in opposite pairs (i, i'): v.u, v.G flip sign, S:(vv - theta I)
         // does not.  With A = w (drho + rho (4.5 (v.u)^2 - 1.5 u^2)), B = 3 w rho v.u,
         // C = 4.5 w S:(vv - theta I), D = 3 w v.G:  f^eq - w rho_ref = A +- B, F = C +- D.
+        // The moving populations are computed first; the rest population takes what is
+        // left of the node's pre-collision mass (sum f^eq = rho, sum F = 0 make this the
+        // same value in exact arithmetic), so mass is conserved up to the rounding of
+        // two sums instead of drifting by (sum of the rounded weights - 1) every step.
         const R third = (R)(1.0 / 3.0);
-        {
-            const R w0 = (R)L::w(0);
-            const R A0 = w0 * (drho - (R)1.5 * r * usq);
-            R SQ0 = -third * Sxx;
-            if constexpr (LAT == 2) SQ0 -= third * Syy;
-            const R C0 = (R)4.5 * w0 * SQ0;
-            post[c][0] = g[c][0] + omega * (A0 - g[c][0]) + C0;
-        }
+        R moved = (R)0;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const int cx = L::vx(i), cy = L::vy(i);
@@ -391,7 +393,12 @@ __device__ __forceinline__ void collide_node(const R (&rho)[N], const R (&lap)[N
             const R D = (R)3 * wi * vG;
             post[c][i] = g[c][i] + omega * (A + B - g[c][i]) + (C + D);
             post[c][ip] = g[c][ip] + omega * (A - B - g[c][ip]) + (C - D);
+            moved += post[c][i] + post[c][ip];
         }
+        R before = (R)0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) before += g[c][i];
+        post[c][0] = before - moved;
     }
 }
 
@@ -552,8 +559,15 @@ __device__ __forceinline__ void step_tile(const S *__restrict__ fin, S *__restri
         }
 }
 
+// FP32 storage with up to two components: ask for five resident 256-thread CTAs per SM
+// (48 registers); more resident warps hide the barrier waits between the phases.
+template <class S, int N, int NT>
+struct MinBlocks {
+    static constexpr int value = (sizeof(S) == 4 && N <= 2 && NT == 256) ? 5 : 1;
+};
+
 template <int LAT, int N, int TX, int TY, class S, class R, int FORCE, int MU>
-__global__ void __launch_bounds__(TX *TY)
+__global__ void __launch_bounds__(TX *TY, MinBlocks<S, N, TX * TY>::value)
     lb_step_kernel(const S *__restrict__ fin, S *__restrict__ fout, DevParams P) {
     step_tile<LAT, N, TX, TY, S, R, FORCE, MU>(fin, fout, P, blockIdx.x * TX, blockIdx.y * TY);
 }

@@ -12,8 +12,18 @@ struct StepLaunch {
     void *fout;
     DevParams P;
     int ncomp, force, tile_x, tile_y;
+    int kernel = LB_KERNEL_TILES;  // lb_kernel_kind, resolved (never AUTO here)
+    int segs = 0;                  // strips: row segments per strip, 0 = fill the GPU once
     cudaStream_t stream;
 };
+
+// Streaming-strip kernel (lb_strip.cuh): strip width and rows per block for N components,
+// and whether a lattice can use it.
+constexpr int STRIP_TX = 32;
+inline int strip_ty(int ncomp) { return ncomp <= 2 ? 8 : 4; }
+inline bool strip_shape_ok(int nx, int ny, int ncomp) {
+    return nx >= STRIP_TX && nx % STRIP_TX == 0 && ny >= strip_ty(ncomp) && ny % strip_ty(ncomp) == 0;
+}
 
 struct FieldLaunch {
     void *f;               // populations (storage type of the precision)
@@ -39,6 +49,8 @@ cudaError_t d1q3_df_step(const StepLaunch &a);
 cudaError_t d2q9_f64_step(const StepLaunch &a);
 cudaError_t d2q9_tbl_step(const StepLaunch &a);
 cudaError_t d2q9_df_step(const StepLaunch &a);
+cudaError_t d2q9_tbl_strip(const StepLaunch &a);
+cudaError_t d2q9_df_strip(const StepLaunch &a);
 
 // field launchers: one per lattice and storage type (double / float)
 #define LBVDW_DECLARE_FIELDS(NAME)                         \

@@ -153,12 +153,15 @@ __device__ __forceinline__ df df_log(df x, const float *s_r, const float *s_hi, 
     q = __fmaf_rn(rh, q, -0.25f);
     q = __fmaf_rn(rh, q, 1.0f / 3.0f);
     float tail = q * (rh * rh * rh);
-    df l1p = df_add(r, df_neg(half_r2));
-    l1p = df_add(l1p, {tail, 0.0f});
-    // e ln 2 + T_j
+    // |r| > |r^2/2| > |tail|: the ordered (quick) sums are exact here
+    df l1p = df_quick(r.hi, -half_r2.hi);
+    l1p = df_quick(l1p.hi, __fadd_rn(l1p.lo, __fsub_rn(r.lo, half_r2.lo)));
+    l1p = df_quick(l1p.hi, __fadd_rn(l1p.lo, tail));
+    // e ln 2 + T_j: |e ln 2| >= ln 2 > |T_j| unless e = 0, when the quick sum is exact too
     df eln2 = df_mul_f({ln2_hi, ln2_lo}, (float)e);
-    df tj = {s_hi[j], s_lo[j]};
-    return df_add(df_add(eln2, tj), l1p);
+    df et = df_quick(eln2.hi, s_hi[j]);
+    et = df_quick(et.hi, __fadd_rn(et.lo, __fadd_rn(eln2.lo, s_lo[j])));
+    return df_add(et, l1p);
 }
 
 }  // namespace lbvdw

@@ -4,6 +4,9 @@
 // step launcher) and, in one unit per storage type, LBVDW_FIELDS (prefix of the
 // init / moments / diagnostics launchers).
 #include "lb_launch.cuh"
+#ifdef LBVDW_STRIPS
+#include "lb_strip.cuh"
+#endif
 
 namespace lbvdw {
 
@@ -88,6 +91,63 @@ cudaError_t LBVDW_CAT(LBVDW_NAME, _step)(const StepLaunch &a) {
     return cudaErrorInvalidConfiguration;
 #endif
 }
+
+#ifdef LBVDW_STRIPS
+
+namespace {
+
+// Opt the kernel in to its dynamic shared memory on the current device and return the
+// CTAs resident per SM times the SM count; `cache` holds one entry per device and must
+// belong to this kernel alone.
+template <class K>
+int strip_slots(K kern, int threads, size_t smem, int (&cache)[64]) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
+    if (cache[dev] > 0) return cache[dev];
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+    int sms = 0, occ = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess) return -1;
+    cache[dev] = sms * (occ > 0 ? occ : 1);
+    return cache[dev];
+}
+
+template <int N, int TY, int FORCE>
+cudaError_t strip_one(const StepLaunch &a) {
+    using Lay = StripLayout<N, STRIP_TX, TY, MUV>;
+    auto kern = lb_strip_kernel<N, STRIP_TX, TY, RV, FORCE, MUV>;
+    static int cache[64];  // one per instantiation, i.e. per kernel
+    const int slots = strip_slots(kern, Lay::NT, Lay::bytes, cache);
+    if (slots < 0) return cudaErrorInvalidConfiguration;
+    const int strips = a.P.nx / STRIP_TX, nblk = a.P.ny / TY;
+    int segs = a.segs > 0 ? a.segs : slots / strips;
+    if (segs < 1) segs = 1;
+    if (segs > nblk) segs = nblk;
+    kern<<<strips * segs, Lay::NT, Lay::bytes, a.stream>>>(static_cast<const float *>(a.fin),
+                                                            static_cast<float *>(a.fout), a.P, segs);
+    return cudaGetLastError();
+}
+
+template <int FORCE>
+cudaError_t strip_n(const StepLaunch &a) {
+    switch (a.ncomp) {
+        case 1: return strip_one<1, 8, FORCE>(a);
+        case 2: return strip_one<2, 8, FORCE>(a);
+        case 3: return strip_one<3, 4, FORCE>(a);
+        case 4: return strip_one<4, 4, FORCE>(a);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t LBVDW_CAT(LBVDW_NAME, _strip)(const StepLaunch &a) {
+    if (!strip_shape_ok(a.P.nx, a.P.ny, a.ncomp) || a.tile_x != STRIP_TX || a.tile_y != strip_ty(a.ncomp))
+        return cudaErrorInvalidConfiguration;
+    return a.force == 1 ? strip_n<1>(a) : strip_n<0>(a);
+}
+
+#endif  // LBVDW_STRIPS
 
 #ifdef LBVDW_FIELDS
 

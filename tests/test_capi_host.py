@@ -54,7 +54,7 @@ def test_status_strings_and_defaults(lib):
     assert capi.status_str(99) == "LB_E_UNKNOWN"
     p = capi.lb_default_params()
     assert p.abi == capi.LBVDW_ABI and p.tau == 1.0 and p.ncomp == 2 and p.lattice == capi.LB_D2Q9
-    assert ctypes.sizeof(capi.lb_params) == 8 * 4 + 8 * 3 + 8 * (16 * 3 + 8) + 4 * 4 + 8
+    assert ctypes.sizeof(capi.lb_params) == 8 * 4 + 8 * 3 + 8 * (16 * 3 + 8) + 4 * 6 + 8
 
 
 def test_null_arguments_are_rejected_without_cuda(lib):
@@ -79,4 +79,21 @@ def test_null_arguments_are_rejected_without_cuda(lib):
     assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID
     p.ncomp = 2
     p.lattice = capi.LB_D1Q3  # ny must be 1
+    assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID
+    # streaming strips: D2Q9 with FP32 storage, nx % 32 == 0, ny % 8 == 0 (1-2 components)
+    p.lattice = capi.LB_D2Q9
+    p.kernel = 3
+    assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID
+    p.kernel = capi.LB_KERNEL_STRIPS                     # FP64 storage has no strips
+    assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID
+    p.precision = capi.LB_FP32_DFMU
+    p.nx = 40
+    assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID
+    p.nx, p.ny = 64, 60
+    assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID
+    p.ny = 64
+    p.tile_x, p.tile_y = 64, 4
+    assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID
+    p.tile_x, p.tile_y = 32, 8
+    p.segments = -1
     assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID

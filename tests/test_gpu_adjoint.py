@@ -108,6 +108,49 @@ def test_adjoint_matches_oracle_finite_differences(gpu_lib, lattice):
     assert abs(np.sum(rb0 * v) - fd_r) <= 1e-6 * abs(fd_r)
 
 
+def final_density(spec, a12, rho0):
+    from paper_1805_07251_gb300 import Simulation
+
+    a = np.array(spec["a"], float).copy()
+    a[0, 1] = a[1, 0] = a12
+    sim = Simulation(lattice=spec["lattice"], nx=spec["nx"], ny=spec["ny"], ncomp=2, tau=spec["tau"],
+                     kT=spec["kT"], gamma_mu=spec["gamma_mu"], a=a, kappa=np.full((2, 2), spec["kappa"]),
+                     lam=spec["lam"], b=spec["b"], precision="fp64")
+    sim.init(rho0)
+    sim.step(spec["steps"])
+    r, _ = sim.moments()
+    sim.close()
+    return r
+
+
+@pytest.mark.parametrize("lattice", ["D1Q3", "D2Q9"])
+def test_one_step_dot_product(gpu_lib, lattice):
+    # <J v, w> = <v, J^T w> for one step (J = d rho_1 / d (rho_0, a12)), with J v from a
+    # Richardson-extrapolated central difference: over one step its truncation and rounding
+    # errors are far below the bar, so this checks the transpose itself
+    from paper_1805_07251_gb300 import Simulation, capi
+
+    spec = spec_small(lattice, 1)
+    rho0 = fields(spec)
+    rng = np.random.default_rng(11)
+    v = 1e-2 * rng.normal(0, 1, rho0.shape)
+    w = rng.normal(0, 1, rho0.shape)
+    sim = Simulation(lattice=spec["lattice"], nx=spec["nx"], ny=spec["ny"], ncomp=2, tau=spec["tau"],
+                     kT=spec["kT"], gamma_mu=spec["gamma_mu"], a=spec["a"], kappa=np.full((2, 2), spec["kappa"]),
+                     lam=spec["lam"], b=spec["b"], precision="fp64")
+    sim.init(rho0)
+    capi.lb_rollout_forward(sim.ctx, 1, 1)
+    rb0, g = capi.lb_rollout_backward(sim.ctx, w, 2)
+    sim.close()
+    a12 = spec["a"][0, 1]
+    jv = central(lambda t: float(np.sum(final_density(spec, a12, rho0 + t * v) * w)), 0.0, 1e-4)
+    assert abs(np.sum(rb0 * v) - jv) <= 1e-8 * abs(jv)
+    # a12 moves rho_1 only weakly (d<rho_1, w>/d a12 ~ 1e-3): a wider step keeps the
+    # quotient's rounding error (~1e-16 |<rho_1, w>| / h) below the bar
+    ja = central(lambda t: float(np.sum(final_density(spec, t, rho0) * w)), a12, 1e-3)
+    assert abs((g[1] + g[2]) - ja) <= 1e-8 * abs(ja)
+
+
 def test_checkpoint_interval_does_not_change_gradients(gpu_lib):
     spec = spec_small("D2Q9", 50)
     rho0, tgt = fields(spec), target(spec)

@@ -122,8 +122,12 @@ def test_fp64_component_counts(gpu_lib, N, lattice):
     sim, orc = make_pair(p)
     rho = lbinputs.uniform_noise_fields(N, ny, nx, 1.3 * x, 1e-2, 2024 + N)
     r_g, j_g, r_o, j_o = run_both(sim, orc, rho, 300)
-    assert rel_err(r_g, r_o) < 1e-12
-    assert np.max(np.abs(j_g - j_o)) < 1e-12 * np.max(np.abs(r_o))
+    # below the critical temperature the mixture phase-separates, which amplifies
+    # rounding differences: the bound is 1e-12 or 100 x the trajectory's own growth
+    # of a one-ulp perturbation, whichever is larger
+    bound = max(1e-12, 100.0 * ulp_amplification(orc, rho, 300))
+    assert rel_err(r_g, r_o) < bound
+    assert np.max(np.abs(j_g - j_o)) < bound * np.max(np.abs(r_o))
 
 
 def test_fp64_nid_force_and_tau(gpu_lib):
@@ -394,3 +398,83 @@ def test_fp32_tile_shapes_identical(gpu_lib):
             outs.append(sim.moments()[0])
         for o in outs[1:]:
             assert np.array_equal(outs[0], o)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed", "fp32_dfmu"])
+def test_four_component_mixture(gpu_lib, precision):
+    # config-4 mixture (random symmetric a_ij, four components) on a small ragged lattice:
+    # one step from the GPU state against the oracle, and the 500-step trajectory bounded
+    # by 1e-12 (FP64) / 1e-5 (FP32) or the conditioning of the trajectory
+    p = lbinputs.base_params("c4")
+    nx, ny = 40, 30
+    sim, orc = make_pair(p, precision=precision, nx=nx, ny=ny)
+    rho = lbinputs.fields("c4", nx=nx, ny=ny)
+    fshape = orc.fshape()
+    sim.init(rho)
+    sim.step(100)
+    if precision == "fp64":
+        f_t = gpu_populations(sim, fshape)
+        sim.step(1)
+        assert np.max(np.abs(gpu_populations(sim, fshape) - orc.run(f_t, 1))) < 1e-14
+    else:
+        f_t = gpu_populations_f32(sim, fshape, rho)
+        sim.step(1)
+        assert np.max(np.abs(gpu_populations_f32(sim, fshape, rho) - orc.run(f_t, 1))) < 2e-6
+    r_g, _, r_o, _ = run_both(sim, orc, rho, 500)
+    if precision == "fp64":
+        assert rel_err(r_g, r_o) < max(1e-12, 100.0 * ulp_amplification(orc, rho, 500))
+    else:
+        assert np.max(np.abs(r_g - r_o)) < max(1e-5, 10.0 * fp32_noise_spread(orc, rho, 500))
+    m0 = rho.reshape(4, -1).sum(axis=1)
+    _, mass, _ = sim.free_energy()
+    assert np.max(np.abs(mass - m0) / m0) < (1e-13 if precision == "fp64" else 1e-6)
+
+
+# ------------------------------------------------------------------ kernel organisations
+
+def strip_case(p, N, nx, ny, precision, force="log", segments=0, steps=40):
+    from paper_1805_07251_gb300 import Simulation
+
+    kw = lbinputs.lib_kwargs(p, nx=nx, ny=ny)
+    if N != kw["ncomp"]:
+        # the first N components of the mixture, above their critical temperature
+        kw.update(ncomp=N, a=kw["a"][:N, :N], kappa=kw["kappa"][:N, :N], lam=kw["lam"][:N, :N], b=kw["b"][:N],
+                  kT=1.1 * lbinputs.one_fluid_critical_kT(kw["a"][:N, :N], kw["b"][:N], np.full(N, 1.0 / N)))
+    rho = lbinputs.fields(p["name"], nx=nx, ny=ny)[:N]
+    outs = []
+    for kernel in ("tiles", "strips"):
+        sim = Simulation(precision=precision, force=force, kernel=kernel, segments=segments, **kw)
+        assert sim.kernel[0] == kernel
+        sim.init(rho)
+        sim.step(steps)
+        outs.append(sim.moments())
+        sim.close()
+    return outs
+
+
+@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32_dfmu"])
+@pytest.mark.parametrize("N,nx,ny", [(1, 64, 48), (2, 32, 8), (2, 96, 40), (3, 64, 36), (4, 32, 4), (4, 96, 20)])
+def test_strip_kernel_is_bitwise_equal_to_tiles(gpu_lib, precision, N, nx, ny):
+    # the streaming-strip organisation computes every node with the same arithmetic in
+    # the same order as the tile kernel (which the rest of this file checks against the
+    # oracle): single strips, single row blocks, wrap-around halos in x and y
+    p = lbinputs.base_params("c4" if N > 2 else "c2")
+    (r_t, j_t), (r_s, j_s) = strip_case(p, N, nx, ny, precision)
+    assert np.array_equal(r_t, r_s) and np.array_equal(j_t, j_s)
+
+
+@pytest.mark.parametrize("segments", [1, 2, 5, 64])
+def test_strip_kernel_segments_and_nid_force(gpu_lib, segments):
+    # any split of the strips into row segments (more segments than row blocks is
+    # clamped), and the "nid" force
+    p = lbinputs.base_params("c2")
+    for force in ("log", "nid"):
+        (r_t, j_t), (r_s, j_s) = strip_case(p, 2, 64, 64, "fp32_dfmu", force=force, segments=segments)
+        assert np.array_equal(r_t, r_s) and np.array_equal(j_t, j_s)
+
+
+def test_strip_kernel_full_size_matches_tiles(gpu_lib):
+    # workload c2 at 1024^2 (the benchmark's launch configuration), 20 steps
+    p = lbinputs.base_params("c2")
+    (r_t, j_t), (r_s, j_s) = strip_case(p, 2, p["nx"], p["ny"], "fp32_dfmu", steps=20)
+    assert np.array_equal(r_t, r_s) and np.array_equal(j_t, j_s)
