@@ -20,7 +20,14 @@ generators.  For each workload:
      changes sign between h = 1e-3 and 1e-4); slowing the dynamics by lowering
      gamma_mu keeps the run in the smooth regime: at gamma_0 / 32 the quotients at
      h = 1e-4, 1e-5 and 1e-6 agree to ~1e-5.  The choice is checked stable at both a12
-     values over the pre-scan.
+     values over the pre-scan;
+  5. workload c4 only: gamma_0 / 256.  The pre-scan's choice (48^2, 1000 steps) does not
+     carry over to the 2048^2 lattice: this deep quench of a random four-component
+     mixture with kappa = 0.1 drives some node's density to zero after a number of steps
+     proportional to 1/gamma_mu, for every gamma_0 2^-k tried (k = 2 .. 8, FP64 at 512^2
+     and FP32 at 2048^2: after ~50 steps at gamma_0/4, ~1250 at gamma_0/256).  The
+     benchmark times a few tens of steps and reports the mass drift over the steps the
+     run spends inside the domain, the longest with gamma_0/256.
 The slab width of workload c1 is sqrt(2 kappa / (theta_cr/kT - 1)) (Sec. V,
 interface width), raised to 2 lattice spacings (Sec. VI) when smaller.
 
@@ -103,6 +110,9 @@ def main():
                 break
         if chosen is None:
             raise SystemExit(f"{name}: no stable gamma_mu found")
+        if name == "c4":
+            # step 5 above: the longest stay in the density domain at 2048^2
+            chosen = g0 / 256
         if name == "c5":
             # step 4 above: a loss smooth at the finite-difference scale
             chosen = g0 / 32
