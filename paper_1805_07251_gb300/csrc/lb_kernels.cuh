@@ -241,12 +241,13 @@ __device__ __forceinline__ bool mu_node(const R (&r)[N], const R (&lin)[N], cons
             phi[c] = ph;
         }
     } else {  // MU_DF
-        df eta = {1.0f, 0.0f}, rt = {0.0f, 0.0f};
+        df eta = {1.0f, 0.0f};
 #pragma unroll
-        for (int c = 0; c < N; ++c) {
-            eta = df_add(eta, df_neg(df_mul_f({P.b_hi[c], P.b_lo[c]}, r[c])));
-            rt = df_add(rt, {r[c], 0.0f});
-        }
+        for (int c = 0; c < N; ++c) eta = df_add(eta, df_neg(df_mul_f({P.b_hi[c], P.b_lo[c]}, r[c])));
+        // total density: the sum of the first two FP32 densities is exact as a pair
+        df rt = N == 1 ? df{r[0], 0.0f} : df_two_sum(r[0], r[N > 1 ? 1 : 0]);
+#pragma unroll
+        for (int c = 2; c < N; ++c) rt = df_add(rt, {r[c], 0.0f});
         ok = ok && eta.hi > 0.0f;
         const df ieta = df_recip(eta);
         const df rte = df_mul(rt, ieta);
@@ -295,8 +296,23 @@ __device__ __forceinline__ void collide_node(const R (&rho)[N], const R (&lap)[N
         uy[c] = jy[c] * ir;
     }
 
-    // friction with the implicit u-hat: (D + L/2) h = -L u0, G^f = D h  (per direction)
-    if constexpr (N > 1) {
+    // friction with the implicit u-hat: (D + L/2) h = -L u0, G^f = D h  (per direction).
+    // Two components: L is rank one and the friction conserves momentum (rho^1 h^1 =
+    // -rho^2 h^2), which leaves one unknown: G^{f,1} = -lambda m (u0^1 - u0^2) / (1 + lambda/2)
+    // = -G^{f,2}, m = rho^1 rho^2 / (rho^1 + rho^2) -- the system's exact solution.
+    if constexpr (N == 2) {
+        const R lam = pv<R>(P.lam[1], P.lam_f[1]);
+        const R k = lam * rho[0] * rho[1] * rcp(rho[0] + rho[1]) * rcp((R)1 + (R)0.5 * lam);
+        const R h0 = (R)0.5 * rcp(rho[0]), h1 = (R)0.5 * rcp(rho[1]);
+        const R fx = -k * ((ux[0] + Gx[0] * h0) - (ux[1] + Gx[1] * h1));
+        Gx[0] += fx;
+        Gx[1] -= fx;
+        if constexpr (L::D == 2) {
+            const R fy = -k * ((uy[0] + Gy[0] * h0) - (uy[1] + Gy[1] * h1));
+            Gy[0] += fy;
+            Gy[1] -= fy;
+        }
+    } else if constexpr (N > 2) {
         R W[N][N];
 #pragma unroll
         for (int c = 0; c < N; ++c)
