@@ -41,9 +41,10 @@
  * Data layout: f[c][i][y][x], rho[c][y][x], mom[c][d][y][x] (d = 0: x, 1: y).
  *
  * Parity status: every function is pinned by the oracle tests (closed forms,
- * invariants, the paper's explicit D1Q3 update, textbook coexistence), except
- * the dynamic role of lambda beyond the uniform-relaxation closed form, which
- * is "parity unpinned".
+ * invariants, the paper's explicit D1Q3 update, textbook coexistence, the
+ * Maxwell-Stefan interdiffusion rate of Sec. IV for the friction lambda), except
+ * lambda's role in nonlinear dynamics (coarsening, interface motion), which is
+ * "parity unpinned".
  */
 #include <math.h>
 #include <stdlib.h>
