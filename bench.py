@@ -70,7 +70,11 @@ def parse():
 # null once they change.
 KERNEL_SOURCES = ("lb_kernels.cuh", "lb_mu.cuh", "lb_tu.cuh", "lb_launch.cuh", "lb_d2q9_df.cu")
 TRAFFIC = {"fp32_dfmu": {"digest": "c9032ef62a65728faea056b1e10a8202be04f52bc44f78a20e2d6c9e5bf3adaa",
-                         "bytes": 108418304, "profile": "profiles/lb_step_kernel_fp32_dfmu_c2_1024.md"}}
+                         "bytes": 108418304, "warp_instructions": 48484352, "issue_active": 0.684,
+                         "profile": "profiles/lb_step_kernel_fp32_dfmu_c2_1024.md"}}
+# instruction issue peak of the GPU: 152 SMs x 4 schedulers x 2.07 GHz (one warp instruction
+# per scheduler per cycle)
+ISSUE_PEAK = 152 * 4 * 2.07e9
 
 
 def kernel_digest():
@@ -88,6 +92,18 @@ def traffic_of(precision):
     if rec and rec["digest"] == kernel_digest():
         return rec["bytes"], rec["profile"]
     return None, None
+
+
+def limiter_of(precision, alg_bytes, peak_gbs):
+    """What bounds the step kernel, from the same ncu capture: its warp instructions per
+    launch at the GPU's peak issue rate, and the HBM fraction that would allow."""
+    rec = TRAFFIC.get(precision)
+    if not rec or rec["digest"] != kernel_digest():
+        return None
+    t_issue = rec["warp_instructions"] / ISSUE_PEAK
+    return {"kind": "instruction issue", "warp_instructions_per_launch": rec["warp_instructions"],
+            "issue_active": rec["issue_active"], "launch_time_at_peak_issue_us": t_issue * 1e6,
+            "hbm_frac_at_peak_issue": alg_bytes / t_issue / 1e9 / peak_gbs, "profile": rec["profile"]}
 
 
 def read_peaks():
@@ -560,7 +576,8 @@ def main():
                      "kernel": "%s<D2Q9, N=2, %s, %s>" % (
                          "lb_strip_kernel" if head["kernel"].startswith("strips") else "lb_step_kernel",
                          head["kernel"].split()[1], HEAD),
-                     "alg_bytes_per_launch": head["alg_bytes"]},
+                     "alg_bytes_per_launch": head["alg_bytes"],
+                     "limiter": limiter_of(HEAD, head["alg_bytes"], peak_gbs)},
         "gpu_launches": head["launches"],
     }
     if e2e is not None:
