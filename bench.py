@@ -41,7 +41,8 @@ UNIT = "component-MLUPS"
 WORKLOAD = "c2"
 FLUSH_BYTES = 256 << 20
 DTYPES = {"fp32_dfmu": "f32 (populations and step), double-float mu",
-          "fp32_mixed": "f32 (populations and step), f64 mu", "fp64": "f64"}
+          "fp32_mixed": "f32 (populations and step), f64 mu", "fp32": "f32 (populations, step and mu)",
+          "fp64": "f64"}
 
 
 def parse():
@@ -59,7 +60,7 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched-sweep measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-rollout measurement")
     ap.add_argument("--no-c4", action="store_true", help="skip the four-component measurement")
-    ap.add_argument("--only", choices=["fp32_dfmu", "fp32_mixed", "fp64"], default=None,
+    ap.add_argument("--only", choices=["fp32_dfmu", "fp32_mixed", "fp32", "fp64"], default=None,
                     help="time one path only (profiling runs): no e2e, no cpu baseline")
     return ap.parse_args()
 
@@ -473,7 +474,7 @@ def main():
     results = {}
     clocks = None
     HEAD = args.only or "fp32_dfmu"
-    paths = [HEAD, "fp32_mixed"] if args.no_fp64 else [HEAD, "fp32_mixed", "fp64"]
+    paths = [HEAD, "fp32_mixed", "fp32"] if args.no_fp64 else [HEAD, "fp32_mixed", "fp32", "fp64"]
     if args.only:
         paths = [args.only]
     for precision in paths:
@@ -593,7 +594,7 @@ def main():
             sweep["vs_fp64_single_run"] = sweep["value"] / results["fp64"]["value"]
         line["batched_sweep"] = sweep
         line["gpu_launches"] += sweep["gpu_launches"]
-    for key, name in (("fp32_mixed", "fp32_fp64mu"), ("fp64", "fp64")):
+    for key, name in (("fp32_mixed", "fp32_fp64mu"), ("fp32", "fp32_fp32mu"), ("fp64", "fp64")):
         if key not in results or key == HEAD:
             continue
         rr = results[key]

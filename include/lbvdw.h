@@ -73,9 +73,12 @@ typedef enum {
     LB_FP32_MIXED = 1, /* FP32 populations stored as deviations f_i - w_i rho_ref^c;
                           FP64 in mu^c (eta, 1/eta, the logarithms -- a table-driven FP64
                           log -- and the differences of mu) and in mass sums */
-    LB_FP32_DFMU = 2   /* as LB_FP32_MIXED, with the FP64 operations of mu^c done in
+    LB_FP32_DFMU = 2,  /* as LB_FP32_MIXED, with the FP64 operations of mu^c done in
                           double-float (pairs of FP32, ~44 significant bits) on the FP32
                           pipe; mass sums stay FP64 */
+    LB_FP32 = 3        /* FP32 populations (deviations) and FP32 mu^c (CUDA's logf): no
+                          FP64-class arithmetic in the step; measures what the FP64 mu of the
+                          two modes above buys.  Single runs only (no batches, no adjoint) */
 } lb_precision;
 
 typedef enum { LB_FORCE_LOG = 0, LB_FORCE_NID = 1 } lb_force_method;

@@ -16,7 +16,7 @@ from . import capi
 __all__ = ["capi", "Simulation", "make_params"]
 
 _LATTICES = {"D1Q3": capi.LB_D1Q3, "D2Q9": capi.LB_D2Q9}
-_PRECISIONS = {"fp64": capi.LB_FP64, "fp32_mixed": capi.LB_FP32_MIXED, "fp32_dfmu": capi.LB_FP32_DFMU}
+_PRECISIONS = {"fp64": capi.LB_FP64, "fp32_mixed": capi.LB_FP32_MIXED, "fp32_dfmu": capi.LB_FP32_DFMU, "fp32": capi.LB_FP32}
 _FORCES = {"log": capi.LB_FORCE_LOG, "nid": capi.LB_FORCE_NID}
 _KERNELS = {"auto": capi.LB_KERNEL_AUTO, "tiles": capi.LB_KERNEL_TILES, "strips": capi.LB_KERNEL_STRIPS}
 

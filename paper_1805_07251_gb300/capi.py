@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "liblbvdw.so")
 LBVDW_ABI = 2
 LB_OK, LB_E_INVALID, LB_E_NOMEM, LB_E_CUDA, LB_E_DOMAIN, LB_E_TIMEOUT, LB_E_STATE = range(7)
 LB_D1Q3, LB_D2Q9 = 1, 2
-LB_FP64, LB_FP32_MIXED, LB_FP32_DFMU = 0, 1, 2
+LB_FP64, LB_FP32_MIXED, LB_FP32_DFMU, LB_FP32 = 0, 1, 2, 3
 LB_FORCE_LOG, LB_FORCE_NID = 0, 1
 LB_KERNEL_AUTO, LB_KERNEL_TILES, LB_KERNEL_STRIPS = 0, 1, 2
 

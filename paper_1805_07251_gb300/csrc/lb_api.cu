@@ -63,8 +63,11 @@ cudaError_t run_step(lb_ctx *c) {
     a.segs = c->p.segments;
     a.stream = c->stream;
     const bool d1 = c->p.lattice == LB_D1Q3;
-    if (a.kernel == LB_KERNEL_STRIPS) return c->p.precision == LB_FP32_MIXED ? d2q9_tbl_strip(a) : d2q9_df_strip(a);
+    if (a.kernel == LB_KERNEL_STRIPS)
+        return c->p.precision == LB_FP32_MIXED ? d2q9_tbl_strip(a)
+                                               : (c->p.precision == LB_FP32 ? d2q9_f32mu_strip(a) : d2q9_df_strip(a));
     switch (c->p.precision) {
+        case LB_FP32: return d1 ? d1q3_f32mu_step(a) : d2q9_f32mu_step(a);
         case LB_FP32_MIXED: return d1 ? d1q3_tbl_step(a) : d2q9_tbl_step(a);
         case LB_FP32_DFMU: return d1 ? d1q3_df_step(a) : d2q9_df_step(a);
         default: return d1 ? d1q3_f64_step(a) : d2q9_f64_step(a);
@@ -240,7 +243,8 @@ lb_status lb_create(const lb_params *p, lb_ctx **out) {
     if (p->abi != LBVDW_ABI) return LB_E_INVALID;
     if (p->lattice != LB_D1Q3 && p->lattice != LB_D2Q9) return LB_E_INVALID;
     if (N < 1 || N > 4) return LB_E_INVALID;
-    if (p->precision != LB_FP64 && p->precision != LB_FP32_MIXED && p->precision != LB_FP32_DFMU)
+    if (p->precision != LB_FP64 && p->precision != LB_FP32_MIXED && p->precision != LB_FP32_DFMU &&
+        p->precision != LB_FP32)
         return LB_E_INVALID;
     if (p->force_method != LB_FORCE_LOG && p->force_method != LB_FORCE_NID) return LB_E_INVALID;
     if (p->nx < 2) return LB_E_INVALID;

@@ -128,22 +128,27 @@ __device__ __forceinline__ T lap_at(const T *s, int ex, int ey, int EXW) {
 //   MU_F64   FP64 path: everything in double, CUDA's log and division;
 //   MU_TBL   mixed path: FP64 eta, 1/eta and table-driven FP64 logs (lb_mu.cuh),
 //            FP32 for the linear part of mu, the stencils and everything after;
-//   MU_DF    mixed path with the FP64 work replaced by double-float arithmetic.
+//   MU_DF    mixed path with the FP64 work replaced by double-float arithmetic;
+//   MU_F32   everything in FP32 (CUDA's logf), the reference point for what the
+//            FP64-class mu of MU_TBL / MU_DF buys.
 // The differences of mu across a node (the only place where mu's extra precision
 // matters) are taken in the mu arithmetic, then rounded to R.
 // ---------------------------------------------------------------------------
-enum { MU_F64 = 0, MU_TBL = 1, MU_DF = 2 };
+enum { MU_F64 = 0, MU_TBL = 1, MU_DF = 2, MU_F32 = 3 };
 
 template <int MU> struct MuStore;
 template <> struct MuStore<MU_F64> { using T = double; };
 template <> struct MuStore<MU_TBL> { using T = double; };
 template <> struct MuStore<MU_DF> { using T = df; };
+template <> struct MuStore<MU_F32> { using T = float; };
 
 // phi difference a - b in the mu arithmetic, rounded to R.  For df values the high
 // parts are subtracted first: exact when they are within a factor 2 (Sterbenz), else
 // rounded once at the precision of the result, which is rounded to FP32 anyway.
 template <class R>
 __device__ __forceinline__ R phi_diff(double a, double b) { return (R)(a - b); }
+template <class R>
+__device__ __forceinline__ R phi_diff(float a, float b) { return (R)(a - b); }
 template <class R>
 __device__ __forceinline__ R phi_diff(df a, df b) {
     return (R)__fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
@@ -238,6 +243,22 @@ __device__ __forceinline__ bool mu_node(const R (&r)[N], const R (&lin)[N], cons
                 ph -= (1.0 / 3.0) * (ok ? log64_tbl((double)r[c], t, t + LOG_TBL, t + 2 * LOG_TBL, P.tbl->ln2_hi_d,
                                                      P.tbl->ln2_lo_d)
                                         : 0.0);
+            phi[c] = ph;
+        }
+    } else if constexpr (MU == MU_F32) {
+        float eta = 1.0f, rt = 0.0f;
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            eta = __fmaf_rn(-P.b_hi[c], (float)r[c], eta);
+            rt += (float)r[c];
+        }
+        ok = ok && eta > 0.0f;
+        const float ieta = 1.0f / eta;
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            const float m = logf((float)r[c] * ieta) + P.b_hi[c] * rt * ieta;
+            float ph = P.gkT_hi * m - P.gamma_hi * (float)lin[c];
+            if constexpr (FORCE == 1) ph -= (1.0f / 3.0f) * logf((float)r[c]);
             phi[c] = ph;
         }
     } else {  // MU_DF

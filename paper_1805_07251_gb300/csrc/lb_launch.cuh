@@ -49,8 +49,11 @@ cudaError_t d1q3_df_step(const StepLaunch &a);
 cudaError_t d2q9_f64_step(const StepLaunch &a);
 cudaError_t d2q9_tbl_step(const StepLaunch &a);
 cudaError_t d2q9_df_step(const StepLaunch &a);
+cudaError_t d1q3_f32mu_step(const StepLaunch &a);
+cudaError_t d2q9_f32mu_step(const StepLaunch &a);
 cudaError_t d2q9_tbl_strip(const StepLaunch &a);
 cudaError_t d2q9_df_strip(const StepLaunch &a);
+cudaError_t d2q9_f32mu_strip(const StepLaunch &a);
 
 // field launchers: one per lattice and storage type (double / float)
 #define LBVDW_DECLARE_FIELDS(NAME)                         \

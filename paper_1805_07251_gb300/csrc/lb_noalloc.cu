@@ -96,7 +96,8 @@ extern "C" lb_status lb_free_energy_noalloc(const lb_params *p, const void *f_de
     const int N = p->ncomp;
     if (p->abi != LBVDW_ABI || N < 1 || N > 4) return LB_E_INVALID;
     if (p->lattice != LB_D1Q3 && p->lattice != LB_D2Q9) return LB_E_INVALID;
-    if (p->precision != LB_FP64 && p->precision != LB_FP32_MIXED && p->precision != LB_FP32_DFMU)
+    if (p->precision != LB_FP64 && p->precision != LB_FP32_MIXED && p->precision != LB_FP32_DFMU &&
+        p->precision != LB_FP32)
         return LB_E_INVALID;
     if (p->nx < 2 || (p->lattice == LB_D1Q3 ? p->ny != 1 : p->ny < 2)) return LB_E_INVALID;
     const size_t n = (size_t)p->nx * (size_t)p->ny;

@@ -306,7 +306,7 @@ def test_chemical_potential_logarithms(gpu_lib):
     assert np.max(np.abs(dfl - ref) / scale) < 2.0 ** -43
 
 
-@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32_dfmu"])
+@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32_dfmu", "fp32"])
 def test_fp32_one_phase_within_1e5_of_fp64_oracle(gpu_lib, precision):
     p = lbinputs.base_params("c2")
     kT = 1.1 * lbinputs.one_fluid_critical_kT(p["a"], p["b"], p["x"])
@@ -319,7 +319,7 @@ def test_fp32_one_phase_within_1e5_of_fp64_oracle(gpu_lib, precision):
     assert np.max(np.abs(mass - m0) / m0) < 1e-6
 
 
-@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32_dfmu"])
+@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32_dfmu", "fp32"])
 def test_fp32_spinodal_step_and_trajectory(gpu_lib, precision):
     # one step from the GPU's own state agrees with the FP64 oracle to FP32 rounding;
     # the 1000-step trajectory is bounded by 1e-5 or by 10x the spread that FP32-size
@@ -356,7 +356,7 @@ def fp32_noise_spread(orc, rho, steps, seed=0):
     return float(np.max(np.abs(r1 - r0)))
 
 
-@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32_dfmu"])
+@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32_dfmu", "fp32"])
 def test_fp32_d1q3_config1(gpu_lib, precision):
     # config 1 (slab with noise) amplifies rounding: one step from the GPU state agrees
     # with the oracle to FP32 rounding; the trajectory bar is 1e-5 or 10x the spread that
@@ -374,7 +374,7 @@ def test_fp32_d1q3_config1(gpu_lib, precision):
     assert np.max(np.abs(r_g - r_o)) < max(1e-5, 10.0 * spread)
 
 
-@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32_dfmu"])
+@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32_dfmu", "fp32"])
 def test_fp32_equilibrium_coexistence_within_1e4(gpu_lib, precision):
     # config 1 (D1Q3 slab) run to equilibrium in FP32 storage and in the FP64 oracle:
     # coexisting bulk densities (averaged over the two sublattices) agree to 1e-4
@@ -452,7 +452,7 @@ def strip_case(p, N, nx, ny, precision, force="log", segments=0, steps=40):
     return outs
 
 
-@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32_dfmu"])
+@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32_dfmu", "fp32"])
 @pytest.mark.parametrize("N,nx,ny", [(1, 64, 48), (2, 32, 8), (2, 96, 40), (3, 64, 36), (4, 32, 4), (4, 96, 20)])
 def test_strip_kernel_is_bitwise_equal_to_tiles(gpu_lib, precision, N, nx, ny):
     # the streaming-strip organisation computes every node with the same arithmetic in
