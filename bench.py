@@ -45,7 +45,7 @@ DTYPES = {"fp32_dfmu": "f32 (populations and step), double-float mu",
           "fp64": "f64"}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--no-c4", action="store_true", help="skip the four-component measurement")
     ap.add_argument("--only", choices=["fp32_dfmu", "fp32_mixed", "fp32", "fp64"], default=None,
                     help="time one path only (profiling runs): no e2e, no cpu baseline")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the headline
@@ -105,6 +105,24 @@ def limiter_of(precision, alg_bytes, peak_gbs):
     return {"kind": "instruction issue", "warp_instructions_per_launch": rec["warp_instructions"],
             "issue_active": rec["issue_active"], "launch_time_at_peak_issue_us": t_issue * 1e6,
             "hbm_frac_at_peak_issue": alg_bytes / t_issue / 1e9 / peak_gbs, "profile": rec["profile"]}
+
+
+def max_over_ranks(dist, value, device):
+    """The largest of the ranks' values (a job lasts as long as its slowest replica);
+    the value itself on a single process."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, seconds):
+    """Whole-job throughput in millions of units per second: every rank processes the same
+    number of units (independent replicas, weak scaling) in at most `seconds`."""
+    return world * units_per_rank / seconds / 1e6
 
 
 def read_peaks():
@@ -267,16 +285,12 @@ def time_sweep(torch, dev, precision, steps, warmup, dist):
     if dist is not None:
         dist.barrier()
     l0 = b.launches
-    ms = b.time_steps(steps)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(dist, b.time_steps(steps), dev)
     launches = b.launches - l0
     unstable = int((b.errors() != 0).sum())
     cn = b.total_component_nodes()
     world = dist.get_world_size() if dist is not None else 1
-    out = {"value": world * cn * steps / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms / steps,
+    out = {"value": job_throughput(world, cn * steps, ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
            "runs": len(recs), "d1q3_runs": sum(r["lattice"] == "D1Q3" for r in recs),
            "d2q9_runs": sum(r["lattice"] == "D2Q9" for r in recs), "component_nodes": cn,
            "tile": "x".join(map(str, tile)) if tile else None, "unstable_runs_after_warmup_and_timed": unstable,
@@ -497,14 +511,10 @@ def main():
             clocks = sampler.stop()
         launches = sim.launches - l0
         per = [a.elapsed_time(b) for a, b in ev]
-        total_ms = float(sum(per))
-        if dist is not None:
-            t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(dist, float(sum(per)), dev)
         kind, tile = sim.kernel
         ms = total_ms / args.steps
-        value = world * N * nodes * args.steps / (total_ms * 1e-3) / 1e6
+        value = job_throughput(world, N * nodes * args.steps, total_ms * 1e-3)
         elem = 8 if precision == "fp64" else 4
         alg_bytes = N * nodes * 9 * 2 * elem
         achieved = alg_bytes / (ms * 1e-3) / 1e9
@@ -546,13 +556,9 @@ def main():
         capi.lb_init_fields(sim.ctx, h_rho)
         sim.step(args.steps)
         capi.lb_read_moments(sim.ctx, o_rho, o_mom)
-        e2e_s = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(dist, time.perf_counter() - t0, dev)
         sim.close()
-        e2e = {"value": world * N * nodes * args.steps / e2e_s / 1e6, "unit": UNIT,
+        e2e = {"value": job_throughput(world, N * nodes * args.steps, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": int(rho.nbytes // args.steps),
                "d2h_bytes_per_step": int((o_rho.nbytes + o_mom.nbytes) // args.steps),
                "note": "per-step bytes amortise one host->device field upload and one device->host "
