@@ -70,8 +70,8 @@ def parse(argv=None):
 # value holds for the kernel sources whose digest is recorded with it and is reported as
 # null once they change.
 KERNEL_SOURCES = ("lb_kernels.cuh", "lb_mu.cuh", "lb_tu.cuh", "lb_launch.cuh", "lb_d2q9_df.cu")
-TRAFFIC = {"fp32_dfmu": {"digest": "81f04d979be8db1eef3abed571a729fa494dea0f32c1de38efbdc21587a61388",
-                         "bytes": 110576640, "warp_instructions": 47284224, "issue_active": 0.680,
+TRAFFIC = {"fp32_dfmu": {"digest": "e2dc21e0f2b6a23c6cbb8e2c9d2f9659c375c5ac442c0d2972d5f05824a8105e",
+                         "bytes": 108601856, "warp_instructions": 48537600, "issue_active": 0.713,
                          "profile": "profiles/lb_step_kernel_fp32_dfmu_c2_1024.md"}}
 # instruction issue peak of the GPU: 152 SMs x 4 schedulers x 2.07 GHz (one warp instruction
 # per scheduler per cycle)
