@@ -355,58 +355,59 @@ static lb_status init_common(lb_ctx *c, const double *rho_dev, const double *mom
     return LB_OK;
 }
 
+// Mean density of each component for the FP32 reference densities (when the caller
+// gave none), through the deterministic diagnostics reduction on the device; the densities
+// are expected in c->rho (copied there from rho_dev when it is another buffer).
+static lb_status device_mean(lb_ctx *c, const double *rho_dev, double *mean) {
+    const int N = c->p.ncomp;
+    bool need_mean = false;
+    if (c->p.precision != LB_FP64)
+        for (int k = 0; k < N; ++k) need_mean = need_mean || !(c->p.rho_ref[k] > 0.0);
+    if (!need_mean) return LB_OK;
+    if (rho_dev != c->rho)
+        LB_CUDA(c, cudaMemcpyAsync(c->rho, rho_dev, sizeof(double) * N * c->n, cudaMemcpyDeviceToDevice, c->stream));
+    LB_CUDA(c, cudaMemsetAsync(c->mom, 0, sizeof(double) * N * c->D * c->n, c->stream));
+    FieldLaunch a = field_args(c);
+    cudaError_t e = run_field(c, 2, a);
+    if (e != cudaSuccess) return cuda_fail(c, e, "diag kernel");
+    c->launches += 2;
+    double h[7];
+    LB_CUDA(c, cudaMemcpyAsync(h, c->diag, sizeof(double) * (N + 3), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < N; ++k) mean[k] = h[k] / (double)c->n;
+    return LB_OK;
+}
+
 lb_status lb_init_fields(lb_ctx *c, const double *rho, const double *mom) {
     if (!c || !rho) return LB_E_INVALID;
     const int N = c->p.ncomp;
     LB_CUDA(c, cudaSetDevice(c->p.device));
-    double mean[4] = {0, 0, 0, 0};
-    for (size_t s = 0; s < c->n; ++s) {
-        double eta = 1.0;
-        for (int k = 0; k < N; ++k) {
-            double r = rho[k * c->n + s];
-            if (!(r > 0.0) || !std::isfinite(r)) {
-                c->has_state = false;
-                return fail(c, LB_E_DOMAIN, "a density is <= 0 or not finite");
-            }
-            eta -= c->p.b[k] * r;
-            mean[k] += r;
-        }
-        if (!(eta > 0.0)) {
-            c->has_state = false;
-            return fail(c, LB_E_DOMAIN, "eta = 1 - sum b rho <= 0 at some node");
-        }
-    }
-    for (int k = 0; k < N; ++k) mean[k] /= (double)c->n;
+    // the fields go to the device first; the reference densities and the domain check
+    // (in the init kernel) are computed there
     LB_CUDA(c, cudaMemcpyAsync(c->rho, rho, sizeof(double) * N * c->n, cudaMemcpyHostToDevice, c->stream));
+    double mean[4] = {0, 0, 0, 0};
+    lb_status s = device_mean(c, c->rho, mean);
+    if (s != LB_OK) return s;
     if (mom)
         LB_CUDA(c, cudaMemcpyAsync(c->mom, mom, sizeof(double) * N * c->D * c->n, cudaMemcpyHostToDevice, c->stream));
-    lb_status s = init_common(c, c->rho, mom ? c->mom : nullptr, mean);
+    s = init_common(c, c->rho, mom ? c->mom : nullptr, mean);
     if (s != LB_OK) return s;
+    unsigned h = 0;
+    LB_CUDA(c, cudaMemcpyAsync(&h, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (h & ERR_DOMAIN) {
+        c->has_state = false;
+        return fail(c, LB_E_DOMAIN, "a density <= 0, eta = 1 - sum b rho <= 0 or a non-finite value in the fields");
+    }
     return LB_OK;
 }
 
 lb_status lb_init_fields_dev(lb_ctx *c, const double *rho_dev, const double *mom_dev) {
     if (!c || !rho_dev) return LB_E_INVALID;
-    const int N = c->p.ncomp;
     LB_CUDA(c, cudaSetDevice(c->p.device));
     double mean[4] = {0, 0, 0, 0};
-    bool need_mean = false;
-    if (c->p.precision != LB_FP64)
-        for (int k = 0; k < N; ++k) need_mean = need_mean || !(c->p.rho_ref[k] > 0.0);
-    if (need_mean) {
-        // mean densities through the diagnostics reduction (one synchronisation)
-        LB_CUDA(c, cudaMemcpyAsync(c->rho, rho_dev, sizeof(double) * N * c->n, cudaMemcpyDeviceToDevice, c->stream));
-        LB_CUDA(c, cudaMemsetAsync(c->mom, 0, sizeof(double) * N * c->D * c->n, c->stream));
-        FieldLaunch a = field_args(c);
-        cudaError_t e = run_field(c, 2, a);
-        if (e != cudaSuccess) return cuda_fail(c, e, "diag kernel");
-        c->launches += 2;
-        double h[7];
-        LB_CUDA(c, cudaMemcpyAsync(h, c->diag, sizeof(double) * (N + 3), cudaMemcpyDeviceToHost, c->stream));
-        LB_CUDA(c, cudaStreamSynchronize(c->stream));
-        for (int k = 0; k < N; ++k) mean[k] = h[k] / (double)c->n;
-    }
+    lb_status s = device_mean(c, rho_dev, mean);
+    if (s != LB_OK) return s;
     return init_common(c, rho_dev, mom_dev, mean);
 }
 
