@@ -60,7 +60,8 @@ def parse(argv=None):
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched-sweep measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-rollout measurement")
     ap.add_argument("--no-c4", action="store_true", help="skip the four-component measurement")
-    ap.add_argument("--only", choices=["fp32_dfmu", "fp32_mixed", "fp32", "fp64"], default=None,
+    ap.add_argument("--only", choices=["fp32_dfmu", "fp32_mixed", "fp32", "fp64", "sweep", "c4", "adjoint"],
+                    default=None,
                     help="time one path only (profiling runs): no e2e, no cpu baseline")
     return ap.parse_args(argv)
 
@@ -487,6 +488,19 @@ def main():
 
     results = {}
     clocks = None
+    if args.only in ("sweep", "c4", "adjoint"):
+        # profiling runs of one secondary workload: its JSON object alone
+        if args.only == "sweep":
+            out = time_sweep(torch, dev, "fp32_dfmu", args.steps, args.warmup, dist)
+        elif args.only == "c4":
+            out = time_c4(torch, dev, "fp32_dfmu", args.steps, args.warmup)
+        else:
+            out = time_adjoint(torch, dev)
+        if rank == 0:
+            print(json.dumps({"only": args.only, **out}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
     HEAD = args.only or "fp32_dfmu"
     paths = [HEAD, "fp32_mixed", "fp32"] if args.no_fp64 else [HEAD, "fp32_mixed", "fp32", "fp64"]
     if args.only:
