@@ -60,7 +60,7 @@ def parse(argv=None):
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched-sweep measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-rollout measurement")
     ap.add_argument("--no-c4", action="store_true", help="skip the four-component measurement")
-    ap.add_argument("--only", choices=["fp32_dfmu", "fp32_mixed", "fp32", "fp64", "sweep", "c4", "adjoint"],
+    ap.add_argument("--only", choices=["fp32_dfmu", "fp32_mixed", "fp32", "fp64", "sweep", "c4", "adjoint", "c1"],
                     default=None,
                     help="time one path only (profiling runs): no e2e, no cpu baseline")
     return ap.parse_args(argv)
@@ -355,6 +355,52 @@ def time_c4(torch, dev, precision, steps, warmup):
             "dtype": DTYPES[precision], "gpu_launches": launches, "l2": "state larger than L2, no flush"}
 
 
+def time_c1(torch, dev, steps):
+    """Workload c1: D1Q3, 2 components, 256 nodes, FP64, the config's 10,000 steps.  So small
+    a lattice is bound by launches, not by the GPU: timed as a single run (one lb_step
+    launch per step) and as a one-run batch (the run resident in shared memory, 32 steps
+    per launch, replayed CUDA graphs), both with CUDA events; mass drift of each."""
+    import numpy as np
+
+    import lbinputs
+    from paper_1805_07251_gb300 import Simulation
+    from paper_1805_07251_gb300.batch import Batch
+
+    p = lbinputs.base_params("c1")
+    kw = lbinputs.lib_kwargs(p)
+    rho = lbinputs.fields("c1")
+    m0 = rho.reshape(2, -1).sum(axis=1)
+    stream = torch.cuda.current_stream(dev)
+    sim = Simulation(precision="fp64", device=dev, stream=stream.cuda_stream, **kw)
+    sim.init(rho)
+    sim.step(100)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    single_s = e0.elapsed_time(e1) * 1e-3
+    _, mass, _ = sim.free_energy()
+    single_drift = float(np.max(np.abs(mass - m0) / m0))
+    sim.close()
+    rec = dict(lattice="D1Q3", nx=p["nx"], ny=1, kT=p["kT"], gamma_mu=p["gamma_mu"])
+    b = Batch([rec], p["a"], p["b"], p["kappa"], p["lam"], 2, tau=p["tau"], precision="fp64", device=dev,
+              stream=stream.cuda_stream)
+    b.init([rho])
+    b.step(96)
+    batch_s = b.time_steps(steps) * 1e-3
+    r, _ = b.read(0)
+    batch_drift = float(np.max(np.abs(r.reshape(2, -1).sum(axis=1) - m0) / m0))
+    b.close()
+    cu = 2 * p["nx"] * steps
+    return {"workload": "D1Q3, 2 components, 256 nodes, FP64, slab (c1)", "steps": steps,
+            "single_run": {"steps_per_s": steps / single_s, "value": cu / single_s / 1e6, "unit": UNIT,
+                           "mass_drift_max_rel": single_drift},
+            "resident_batch_of_one": {"steps_per_s": steps / batch_s, "value": cu / batch_s / 1e6, "unit": UNIT,
+                                      "mass_drift_max_rel": batch_drift}}
+
+
 def richardson(fun, x0, h):
     """Central difference with step h, extrapolated twice (h, h/2, h/4): O(h^6)."""
     d = [(fun(x0 + s) - fun(x0 - s)) / (2 * s) for s in (h, h / 2, h / 4)]
@@ -488,12 +534,14 @@ def main():
 
     results = {}
     clocks = None
-    if args.only in ("sweep", "c4", "adjoint"):
+    if args.only in ("sweep", "c4", "adjoint", "c1"):
         # profiling runs of one secondary workload: its JSON object alone
         if args.only == "sweep":
             out = time_sweep(torch, dev, "fp32_dfmu", args.steps, args.warmup, dist)
         elif args.only == "c4":
             out = time_c4(torch, dev, "fp32_dfmu", args.steps, args.warmup)
+        elif args.only == "c1":
+            out = time_c1(torch, dev, 10000)
         else:
             out = time_adjoint(torch, dev)
         if rank == 0:
@@ -539,6 +587,7 @@ def main():
     sweep = None
     if not args.only and not args.no_sweep:
         sweep = time_sweep(torch, dev, HEAD, args.steps, args.warmup, dist)
+    c1 = time_c1(torch, dev, 10000) if not args.only and rank == 0 else None
     c4 = None
     if not args.only and not args.no_c4:
         c4 = time_c4(torch, dev, HEAD, args.steps, args.warmup)
@@ -605,6 +654,8 @@ def main():
         line["e2e"] = e2e
     if adjoint is not None:
         line["adjoint_rollout"] = adjoint
+    if c1 is not None:
+        line["c1_small_lattice"] = c1
     if c4 is not None:
         c4["roofline_hbm"].update({"peak": peak_gbs, "unit": "GB/s", "frac": c4["roofline_hbm"]["achieved"] / peak_gbs})
         line["four_components"] = c4
