@@ -143,9 +143,10 @@ lb_status lb_create(const lb_params *p, lb_ctx **out);
 
 /* Set the state to the equilibrium (Eq. feq, at theta = 1/3) of host densities
  * rho [c][y][x] and momenta mom [c][d][y][x] (bare rho^c u^c; NULL = at rest).
- * Synchronous.  Clears the error word and the poisoned flag.
- * Errors: LB_E_INVALID (NULL ctx/rho), LB_E_DOMAIN (a density <= 0 or eta <= 0:
- * the state is left unset), LB_E_CUDA. */
+ * Synchronous.  Clears the error word and the poisoned flag.  The fields are copied to
+ * the device first; their check and (FP32 storage without rho_ref) their mean run there.
+ * Errors: LB_E_INVALID (NULL ctx/rho), LB_E_DOMAIN (a density <= 0 or not finite, or
+ * eta <= 0 at some node: the state is left unset), LB_E_CUDA. */
 lb_status lb_init_fields(lb_ctx *ctx, const double *rho, const double *mom);
 
 /* Same as lb_init_fields with device pointers (FP64, same layouts), enqueued on the
