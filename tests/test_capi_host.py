@@ -97,3 +97,18 @@ def test_null_arguments_are_rejected_without_cuda(lib):
     p.tile_x, p.tile_y = 32, 8
     p.segments = -1
     assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID
+
+
+def test_batches_reject_the_fp32_mu_precision_without_cuda(lib):
+    # LB_FP32 (FP32 mu) serves single runs only; a batch asking for it is refused
+    # before any CUDA call
+    from paper_1805_07251_gb300 import capi
+
+    p = capi.lb_default_params()
+    p.b[0] = p.b[1] = 0.3
+    p.precision = capi.LB_FP32
+    runs = (capi.lb_run_desc * 1)()
+    runs[0].lattice, runs[0].nx, runs[0].ny, runs[0].kT, runs[0].gamma_mu = capi.LB_D2Q9, 64, 64, 1.0 / 3.0, 0.1
+    out = ctypes.c_void_p()
+    assert lib.lb_batch_create(ctypes.byref(p), runs, 1, ctypes.byref(out)) == capi.LB_E_INVALID
+    assert lib.lb_batch_create(None, runs, 1, ctypes.byref(out)) == capi.LB_E_INVALID
