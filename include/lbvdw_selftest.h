@@ -1,8 +1,8 @@
 /*
- * lbvdw_selftest.h -- self-test entry point of the lbvdw library (not part of the
- * lattice Boltzmann step).  It exposes the two logarithms the chemical-potential
- * stage uses on GB300 so that tests can compare them with CUDA's double-precision
- * log on the same device:
+ * lbvdw_selftest.h -- self-test entry points of the lbvdw library (not part of the
+ * lattice Boltzmann step).  lb_selftest_log exposes the two logarithms the
+ * chemical-potential stage uses on GB300 so that tests can compare them with CUDA's
+ * double-precision log on the same device:
  *   - the table-driven FP64 logarithm of the LB_FP32_MIXED path;
  *   - the double-float logarithm of the LB_FP32_DFMU path.
  * The chemical potential that needs these logarithms is Eq. discreteChemicalPotential
@@ -27,6 +27,15 @@ extern "C" {
  * LB_E_NOMEM, LB_E_CUDA. */
 lb_status lb_selftest_log(int32_t device, const double *x, int64_t n, double *out_tbl, double *out_df,
                           double *out_ref);
+
+/* The bounded wait that the streaming-strip kernel (LB_KERNEL_STRIPS) applies to its
+ * bulk-copy barriers, run on one CTA of 64 threads on device `device` against an mbarrier
+ * that completes (arrive != 0: thread 0 arrives) or that nothing ever completes
+ * (arrive == 0).  Every thread polls at most `polls` times; *flag receives the error word:
+ * 0 when the barrier completed, 2 (the timeout bit, reported as LB_E_TIMEOUT by the step
+ * calls) when the polls ran out.  No fault, no hang: the wait ends either way.
+ * Synchronous.  Errors: LB_E_INVALID (NULL flag, polls < 1), LB_E_NOMEM, LB_E_CUDA. */
+lb_status lb_selftest_wait(int32_t device, uint32_t polls, int32_t arrive, uint32_t *flag);
 
 #ifdef __cplusplus
 }

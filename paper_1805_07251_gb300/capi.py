@@ -101,6 +101,8 @@ def load():
         "lb_status_str": (ctypes.c_char_p, [ctypes.c_int]),
         "lb_last_error": (ctypes.c_char_p, [C]),
         "lb_selftest_log": (ctypes.c_int, [ctypes.c_int32, _DP, ctypes.c_int64, _DP, _DP, _DP]),
+        "lb_selftest_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.c_uint32, ctypes.c_int32,
+                                            ctypes.POINTER(ctypes.c_uint32)]),
         "lb_free_energy_noalloc": (ctypes.c_int, [P, C, C]),
         "lb_batch_create": (ctypes.c_int, [P, ctypes.POINTER(lb_run_desc), ctypes.c_int32, ctypes.POINTER(C)]),
         "lb_batch_init": (ctypes.c_int, [C, _DP]),
@@ -223,6 +225,14 @@ def lb_destroy(ctx):
 
 def lb_last_error(ctx):
     return load().lb_last_error(ctx).decode()
+
+
+def lb_selftest_wait(device, polls, arrive):
+    flag = ctypes.c_uint32(0)
+    rc = load().lb_selftest_wait(int(device), int(polls), int(arrive), ctypes.byref(flag))
+    if rc != LB_OK:
+        raise LBError(rc, "lb_selftest_wait")
+    return int(flag.value)
 
 
 def lb_selftest_log(device, x):

@@ -3,6 +3,7 @@
 #include <cstring>
 
 #include "lb_kernels.cuh"
+#include "lb_strip.cuh"
 #include "lbvdw_selftest.h"
 
 namespace lbvdw {
@@ -23,7 +24,45 @@ __global__ void selftest_log_kernel(const double *x, long long n, const lbvdw::L
     o_ref[k] = log(v);
 }
 
+// The bounded mbarrier wait of the streaming-strip kernel on a barrier that completes
+// (thread 0 arrives) or never does (nobody arrives): the wait must end either way and
+// report the second case in the flag.
+__global__ void selftest_wait_kernel(unsigned *flag, unsigned polls, int arrive) {
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) {
+        lbvdw::mbar_init(&bar, 1);
+        lbvdw::fence_barrier_init();
+    }
+    __syncthreads();
+    if (arrive && threadIdx.x == 0)
+        asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(
+                         lbvdw::smem_addr(&bar))
+                     : "memory");
+    if (!lbvdw::mbar_wait_bounded(&bar, 0, polls)) atomicOr(flag, lbvdw::ERR_TIMEOUT);
+}
+
 }  // namespace
+
+extern "C" lb_status lb_selftest_wait(int32_t device, uint32_t polls, int32_t arrive, uint32_t *flag) {
+    if (!flag || polls < 1) return LB_E_INVALID;
+    if (cudaSetDevice(device) != cudaSuccess) return LB_E_CUDA;
+    unsigned *d = nullptr;
+    if (cudaMalloc(&d, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return LB_E_NOMEM;
+    }
+    lb_status st = LB_OK;
+    if (cudaMemset(d, 0, sizeof(unsigned)) != cudaSuccess) {
+        st = LB_E_CUDA;
+    } else {
+        selftest_wait_kernel<<<1, 64>>>(d, polls, arrive);
+        if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+            cudaMemcpy(flag, d, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = LB_E_CUDA;
+    }
+    cudaFree(d);
+    return st;
+}
 
 extern "C" lb_status lb_selftest_log(int32_t device, const double *x, int64_t n, double *out_tbl, double *out_df,
                                      double *out_ref) {
