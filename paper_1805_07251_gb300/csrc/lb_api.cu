@@ -155,8 +155,10 @@ namespace lbvdw {
 // Tables of the table-driven logarithms (lb_mu.cuh).  c_j = 1 + j/128; r_j = 1/c_j
 // rounded to the working type; T_j = -ln(r_j) in extended precision, split into
 // hi + lo.  ln 2 comes from its decimal expansion.
+constexpr const char *LN2_DIGITS = "0.69314718055994530941723212145817656807550013436";
+
 void fill_log_tables(LogTables *t) {
-    const long double ln2 = strtold("0.69314718055994530941723212145817656807550013436", nullptr);
+    const long double ln2 = strtold(LN2_DIGITS, nullptr);
     for (int j = 0; j < LOG_TBL; ++j) {
         long double cj = 1.0L + (long double)j / LOG_TBL;
         double r64 = (double)(1.0L / cj);
@@ -166,9 +168,8 @@ void fill_log_tables(LogTables *t) {
         t->t64_lo[j] = (double)(T64 - (long double)t->t64_hi[j]);
         float r32 = (float)(1.0L / cj);
         long double T32 = -logl((long double)r32);
-        t->r32[j] = r32;
-        t->t32_hi[j] = (float)T32;
-        t->t32_lo[j] = (float)(T32 - (long double)t->t32_hi[j]);
+        const float t32_hi = (float)T32;
+        t->t32[j] = make_float4(r32, t32_hi, (float)(T32 - (long double)t32_hi), 0.0f);
     }
     // FP64 hi: ln 2 with its low 21 significand bits cleared (e * hi exact for |e| < 2^10)
     double h = (double)ln2;
@@ -215,6 +216,13 @@ void make_dev_params(const lb_params &p, DevParams &d, unsigned *err, const LogT
     d.omega_f = (float)d.omega;
     d.psi_g_f = (float)d.psi_g;
     d.psi_l_f = (float)d.psi_l;
+    d.omc = 1.0 - d.omega;
+    d.omc_f = (float)d.omc;
+    d.lam_fr = p.lambda[1] / (1.0 + 0.5 * p.lambda[1]);
+    d.lam_fr_f = (float)d.lam_fr;
+    const long double ln2 = strtold(LN2_DIGITS, nullptr);
+    d.ln2_hi_f = (float)ln2;
+    d.ln2_lo_f = (float)(ln2 - (long double)d.ln2_hi_f);
 }
 
 }  // namespace lbvdw

@@ -40,7 +40,7 @@ template <int N, class S, class R, int MU>
 __host__ __device__ constexpr size_t resident_smem_bytes(int L) {
     using MT = typename MuStore<MU>::T;
     return sizeof(S) * (size_t)N * 3 * L + sizeof(R) * (size_t)N * (L + 4) + sizeof(MT) * (size_t)N * (L + 2) +
-           sizeof(float) * 3 * LOG_TBL * 2 + 64;
+           sizeof(float) * TblWords<MU>::value + 64;
 }
 
 template <int N, class S, class R, int FORCE, int MU>
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(RESIDENT_THREADS)
     extern __shared__ __align__(16) unsigned char smem[];
     // layout: tables | phi [N][L+2] | rho [N][L+4] | f [N][3][L]
     float *s_tbl = reinterpret_cast<float *>(smem);
-    MT *s_phi = reinterpret_cast<MT *>(smem + sizeof(float) * 3 * LOG_TBL * 2);
+    MT *s_phi = reinterpret_cast<MT *>(smem + sizeof(float) * TblWords<MU>::value);
     R *s_rho = reinterpret_cast<R *>(reinterpret_cast<unsigned char *>(s_phi) + sizeof(MT) * (size_t)N * (L + 2));
     S *s_f = reinterpret_cast<S *>(reinterpret_cast<unsigned char *>(s_rho) + sizeof(R) * (size_t)N * (L + 4));
     const int PH = L + 2, RH = L + 4;
@@ -79,30 +79,23 @@ __global__ void __launch_bounds__(RESIDENT_THREADS)
             xx = xx < 0 ? xx + L : (xx >= L ? xx - L : xx);
 #pragma unroll
             for (int c = 0; c < N; ++c) {
-                R acc = (R)0;
+                R acc = (R)s_f[(c * Q) * L + xx];
 #pragma unroll
-                for (int i = 0; i < Q; ++i) acc += (R)s_f[(c * Q + i) * L + xx];
-                s_rho[c * RH + k] = pv<R>(P.rho_ref[c], P.rho_ref_f[c]) + acc;
+                for (int i = 1; i < Q; ++i) acc = v_add(acc, (R)s_f[(c * Q + i) * L + xx]);
+                s_rho[c * RH + k] = v_add(pv<R>(P.rho_ref[c], P.rho_ref_f[c]), acc);
             }
         }
         __syncthreads();
         // chemical potentials on the run plus a 1-node ring
         for (int k = tid; k < PH; k += NT) {
             const int ex = k + 1;
-            R r[N], lin[N];
+            R r[N], lp[N], lin[N];
 #pragma unroll
             for (int c = 0; c < N; ++c) {
                 r[c] = s_rho[c * RH + ex];
-                lin[c] = (R)0;
+                lp[c] = lap_at<1, R>(s_rho + c * RH, ex, 0, RH);
             }
-#pragma unroll
-            for (int cc = 0; cc < N; ++cc) {
-                R lp = lap_at<1, R>(s_rho + cc * RH, ex, 0, RH);
-#pragma unroll
-                for (int c = 0; c < N; ++c)
-                    lin[c] += pv<R>(2.0 * P.a[c * 4 + cc], P.a2_f[c * 4 + cc]) * r[cc] +
-                              pv<R>(P.kappa[c * 4 + cc], P.kappa_f[c * 4 + cc]) * lp;
-            }
+            lin_node<N, R>(r, lp, P, lin);
             MT phi[N];
             if (!mu_node<N, R, FORCE, MU>(r, lin, P, s_tbl, phi)) bad = 1;
 #pragma unroll
@@ -124,15 +117,10 @@ __global__ void __launch_bounds__(RESIDENT_THREADS)
                 grad_phi<1, R, MT>(s_phi + c * PH, mx, 0, PH, gpx[c], gpy[c]);
                 if constexpr (FORCE == 0) grad_at<1, R>(s_rho + c * RH, ex, 0, RH, grx[c], gry[c]);
                 else grx[c] = gry[c] = (R)0;
-                R ax = (R)0;
+                R acc;
 #pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    gr[c][i] = (R)s_f[(c * Q + i) * L + x];
-                    if (L1::vx(i) == 1) ax += gr[c][i];
-                    if (L1::vx(i) == -1) ax -= gr[c][i];
-                }
-                jx[c] = ax;
-                jy[c] = (R)0;
+                for (int i = 0; i < Q; ++i) gr[c][i] = (R)s_f[(c * Q + i) * L + x];
+                moments_lane<1>(gr[c], acc, jx[c], jy[c]);
             }
             collide_node<1, N, R, FORCE>(rho, lap, gpx, gpy, grx, gry, jx, jy, P, gr, post[m]);
         }

@@ -16,6 +16,7 @@
 // carried in FP64 (MU_TBL) or in double-float arithmetic (MU_DF), see lb_mu.cuh.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "lb_mu.cuh"
@@ -42,6 +43,10 @@ struct DevParams {
     // FP32 copies for the FP32 paths (no double->float conversion in the kernels)
     float a2_f[16], kappa_f[16], lam_f[16];  // 2 a, kappa, lambda
     float rho_ref_f[4], omega_f, psi_g_f, psi_l_f;
+    // 1 - omega, and lambda^12 / (1 + lambda^12 / 2) of the two-component friction
+    double omc, lam_fr;
+    float omc_f, lam_fr_f;
+    float ln2_hi_f, ln2_lo_f;  // ln 2 as a double-float (the df logarithm)
 };
 
 // a parameter in the compute type R: the double value or its precomputed float copy
@@ -92,33 +97,28 @@ __device__ __forceinline__ size_t pop_index(int c, int i, int Q, int y, int x, i
     return ((size_t)(c * Q + i) * (size_t)ny + (size_t)y) * (size_t)nx + (size_t)x;
 }
 
-// Stencils on a shared-memory array with row length EXW.
-// D1Q3: central difference (phi+ - phi-)/2 and Lap = phi+ + phi- - 2 phi (Sec. V).
-// D2Q9: D = (1/theta) sum w_i v_i phi_i, Lap = (2/theta) sum w_i (phi_i - phi_0).
+// Stencils on a shared-memory array with row length EXW (the formulas are in lb_lane.cuh).
+template <class T>
+__device__ __forceinline__ Nbr9<T> nbr9(const T *p, int W) {
+    return {p[0], p[1], p[-1], p[W], p[-W], p[W + 1], p[W - 1], p[-W - 1], p[-W + 1]};
+}
+
 template <int LAT, class T>
 __device__ __forceinline__ void grad_at(const T *s, int ex, int ey, int EXW, T &gx, T &gy) {
     const T *p = s + ey * EXW + ex;
     if constexpr (LAT == 1) {
-        gx = (T)0.5 * (p[1] - p[-1]);
-        gy = (T)0;
+        gx = grad_d1q3(p[1], p[-1]);
+        gy = vc<T>(0.0);
     } else {
-        T e = p[1], wv = p[-1], n = p[EXW], sv = p[-EXW];
-        T ne = p[EXW + 1], nw = p[EXW - 1], sw = p[-EXW - 1], se = p[-EXW + 1];
-        gx = (e - wv) * (T)(1.0 / 3.0) + ((ne + se) - (nw + sw)) * (T)(1.0 / 12.0);
-        gy = (n - sv) * (T)(1.0 / 3.0) + ((ne + nw) - (se + sw)) * (T)(1.0 / 12.0);
+        grad_d2q9(nbr9(p, EXW), gx, gy);
     }
 }
 
 template <int LAT, class T>
 __device__ __forceinline__ T lap_at(const T *s, int ex, int ey, int EXW) {
     const T *p = s + ey * EXW + ex;
-    if constexpr (LAT == 1) {
-        return (p[1] + p[-1]) - (T)2 * p[0];
-    } else {
-        T axis = (p[1] + p[-1]) + (p[EXW] + p[-EXW]);
-        T diag = (p[EXW + 1] + p[EXW - 1]) + (p[-EXW + 1] + p[-EXW - 1]);
-        return axis * (T)(2.0 / 3.0) + diag * (T)(1.0 / 6.0) - p[0] * (T)(10.0 / 3.0);
-    }
+    if constexpr (LAT == 1) return lap_d1q3(p[0], p[1], p[-1]);
+    else return lap_d2q9(nbr9(p, EXW));
 }
 
 // ---------------------------------------------------------------------------
@@ -148,10 +148,12 @@ template <> struct MuStore<MU_F32> { using T = float; };
 template <class R>
 __device__ __forceinline__ R phi_diff(double a, double b) { return (R)(a - b); }
 template <class R>
-__device__ __forceinline__ R phi_diff(float a, float b) { return (R)(a - b); }
+__device__ __forceinline__ R phi_diff(float a, float b) { return (R)__fsub_rn(a, b); }
 template <class R>
-__device__ __forceinline__ R phi_diff(df a, df b) {
-    return (R)__fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
+__device__ __forceinline__ R phi_diff(df a, df b) { return v_add(v_sub(a.hi, b.hi), v_sub(a.lo, b.lo)); }
+__device__ __forceinline__ float2 phi_diff2(float2 a, float2 b) { return v_sub(a, b); }
+__device__ __forceinline__ float2 phi_diff2(DF<float2> a, DF<float2> b) {
+    return v_add(v_sub(a.hi, b.hi), v_sub(a.lo, b.lo));
 }
 
 // D phi at (mx, my) of an MX-wide shared array, differences in the mu arithmetic
@@ -159,22 +161,20 @@ template <int LAT, class R, class T>
 __device__ __forceinline__ void grad_phi(const T *s, int mx, int my, int MXW, R &gx, R &gy) {
     const T *p = s + my * MXW + mx;
     if constexpr (LAT == 1) {
-        gx = (R)0.5 * phi_diff<R>(p[1], p[-1]);
-        gy = (R)0;
+        gx = v_mul(phi_diff<R>(p[1], p[-1]), vc<R>(0.5));
+        gy = vc<R>(0.0);
     } else {
-        R ew = phi_diff<R>(p[1], p[-1]);
-        R ns = phi_diff<R>(p[MXW], p[-MXW]);
-        R d1 = phi_diff<R>(p[MXW + 1], p[-MXW - 1]);  // NE - SW
-        R d2 = phi_diff<R>(p[-MXW + 1], p[MXW - 1]);  // SE - NW
-        gx = ew * (R)(1.0 / 3.0) + (d1 + d2) * (R)(1.0 / 12.0);
-        gy = ns * (R)(1.0 / 3.0) + (d1 - d2) * (R)(1.0 / 12.0);
+        grad_d2q9_diff(phi_diff<R>(p[1], p[-1]), phi_diff<R>(p[MXW], p[-MXW]),
+                       phi_diff<R>(p[MXW + 1], p[-MXW - 1]),  // NE - SW
+                       phi_diff<R>(p[-MXW + 1], p[MXW - 1]),  // SE - NW
+                       gx, gy);
     }
 }
 
 // shared-memory log tables of the MU variant (TBL_WORDS floats)
 template <int MU>
 struct TblWords {
-    static constexpr int value = MU == MU_TBL ? 3 * LOG_TBL * 2 : (MU == MU_DF ? 3 * LOG_TBL : 1);
+    static constexpr int value = MU == MU_TBL ? 3 * LOG_TBL * 2 : (MU == MU_DF ? 4 * LOG_TBL : 4);
 };
 
 template <int MU>
@@ -187,12 +187,115 @@ __device__ __forceinline__ void load_tables(float *s_tbl, const DevParams &P, in
             t[2 * LOG_TBL + k] = P.tbl->t64_lo[k];
         }
     } else if constexpr (MU == MU_DF) {
-        for (int k = tid; k < LOG_TBL; k += nt) {
-            s_tbl[k] = P.tbl->r32[k];
-            s_tbl[LOG_TBL + k] = P.tbl->t32_hi[k];
-            s_tbl[2 * LOG_TBL + k] = P.tbl->t32_lo[k];
+        float4 *t = reinterpret_cast<float4 *>(s_tbl);
+        for (int k = tid; k < LOG_TBL; k += nt) t[k] = P.tbl->t32[k];
+    }
+}
+
+// Moments of one node's populations (deviations): sum_i g_i and the bare momentum
+// sum_i g_i v_i, summed in direction order.
+template <int LAT, class V>
+__device__ __forceinline__ void moments_lane(const V (&g)[Lat<LAT>::Q], V &acc, V &ax, V &ay) {
+    using L = Lat<LAT>;
+    acc = g[0];
+    bool fx = true, fy = true;
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+        acc = v_add(acc, g[i]);
+        if (L::vx(i) != 0) {
+            const V t = L::vx(i) == 1 ? g[i] : v_neg(g[i]);
+            ax = fx ? t : v_add(ax, t);
+            fx = false;
+        }
+        if (L::vy(i) != 0) {
+            const V t = L::vy(i) == 1 ? g[i] : v_neg(g[i]);
+            ay = fy ? t : v_add(ay, t);
+            fy = false;
         }
     }
+    if (fy) ay = vc<V>(0.0);
+}
+
+// The linear part of mu^c: lin^c = sum_c' (kappa^{cc'} Lap rho^c' + 2 a^{cc'} rho^c'),
+// c' ascending (Eq. discreteChemicalPotential).
+template <int N, class R>
+__device__ __forceinline__ void lin_node(const R (&r)[N], const R (&lp)[N], const DevParams &P, R (&lin)[N]) {
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        R t = v_mul(pv<R>(P.kappa[c * 4], P.kappa_f[c * 4]), lp[0]);
+        t = v_fma(pv<R>(2.0 * P.a[c * 4], P.a2_f[c * 4]), r[0], t);
+#pragma unroll
+        for (int cc = 1; cc < N; ++cc) {
+            t = v_fma(pv<R>(P.kappa[c * 4 + cc], P.kappa_f[c * 4 + cc]), lp[cc], t);
+            t = v_fma(pv<R>(2.0 * P.a[c * 4 + cc], P.a2_f[c * 4 + cc]), r[cc], t);
+        }
+        lin[c] = t;
+    }
+}
+// the same for a two-component pair, both components in one lane pair
+__device__ __forceinline__ float2 lin_pair(float2 r, float2 lp, const DevParams &P) {
+    float2 t = v_mul(make_float2(P.kappa_f[0], P.kappa_f[4]), vs(lp.x, r));
+    t = v_fma(make_float2(P.a2_f[0], P.a2_f[4]), vs(r.x, r), t);
+    t = v_fma(make_float2(P.kappa_f[1], P.kappa_f[5]), vs(lp.y, r), t);
+    return v_fma(make_float2(P.a2_f[1], P.a2_f[5]), vs(r.y, r), t);
+}
+
+// ---------------------------------------------------------------------------
+// chemical potential in FP32 storage: phi^c = gamma mu^c (minus theta ln rho^c for "nid")
+// with mu^c = kT [ln(rho^c / eta) + b^c rho / eta] - lin^c (Eq. discreteChemicalPotential).
+// eta and rho / eta are one value per node; the rest runs per component lane.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float v_log(float x) { return logf(x); }
+__device__ __forceinline__ float2 v_log(float2 x) { return make_float2(logf(x.x), logf(x.y)); }
+
+template <class V, int FORCE>
+__device__ __forceinline__ DF<V> mu_df_lanes(V r, V lin, DF<V> b, df ieta, df rte, bool ok, const DevParams &P,
+                                             const float4 *s_t) {
+    const V zero = vc<V>(0.0);
+    DF<V> lg = df_log(df_mul_f(df_splat(ieta, r), r), s_t, P.ln2_hi_f, P.ln2_lo_f);
+    if (!ok) lg = DF<V>{zero, zero};
+    const DF<V> m = df_add(lg, df_mul(df_splat(rte, r), b));
+    DF<V> ph = df_add(df_mul(m, df_splat(df{P.gkT_hi, P.gkT_lo}, r)),
+                      df_neg(df_mul_f(df_splat(df{P.gamma_hi, P.gamma_lo}, r), lin)));
+    if constexpr (FORCE == 1) {
+        DF<V> lr = df_log(DF<V>{r, zero}, s_t, P.ln2_hi_f, P.ln2_lo_f);
+        if (!ok) lr = DF<V>{zero, zero};
+        ph = df_add(ph, df_neg(df_mul_f(lr, vc<V>(1.0 / 3.0))));
+    }
+    return ph;
+}
+
+template <class V, int FORCE>
+__device__ __forceinline__ V mu_f32_lanes(V r, V lin, V b, float ieta, float rte, const DevParams &P) {
+    const V lg = v_log(v_mul(r, vs(ieta, r)));
+    V ph = v_fma(vs(P.gkT_hi, r), v_fma(b, vs(rte, r), lg), v_mul(vs(-P.gamma_hi, r), lin));
+    if constexpr (FORCE == 1) ph = v_fma(vc<V>(-1.0 / 3.0), v_log(r), ph);
+    return ph;
+}
+
+// two components, double-float mu: phi of both lanes; false outside the domain
+template <int FORCE>
+__device__ __forceinline__ bool mu_pair_df(float2 r, float2 lin, const DevParams &P, const float4 *s_t,
+                                           DF<float2> &phi) {
+    const DF<float2> b = {make_float2(P.b_hi[0], P.b_hi[1]), make_float2(P.b_lo[0], P.b_lo[1])};
+    const DF<float2> br = df_mul_f(b, r);
+    df eta = df_add(df{1.0f, 0.0f}, df_neg(df{br.hi.x, br.lo.x}));
+    eta = df_add(eta, df_neg(df{br.hi.y, br.lo.y}));
+    const df rt = df_two_sum(r.x, r.y);  // the sum of two FP32 densities is exact as a pair
+    const bool ok = r.x > 0.0f && r.y > 0.0f && eta.hi > 0.0f;
+    const df ieta = df_recip(eta);
+    phi = mu_df_lanes<float2, FORCE>(r, lin, b, ieta, df_mul(rt, ieta), ok, P, s_t);
+    return ok;
+}
+
+template <int FORCE>
+__device__ __forceinline__ bool mu_pair_f32(float2 r, float2 lin, const DevParams &P, float2 &phi) {
+    const float eta = __fmaf_rn(-P.b_hi[1], r.y, __fmaf_rn(-P.b_hi[0], r.x, 1.0f));
+    const bool ok = r.x > 0.0f && r.y > 0.0f && eta > 0.0f;
+    const float ieta = 1.0f / eta;
+    phi = mu_f32_lanes<float2, FORCE>(r, lin, make_float2(P.b_hi[0], P.b_hi[1]), ieta,
+                                      __fmul_rn(__fadd_rn(r.x, r.y), ieta), P);
+    return ok;
 }
 
 // One node of phase 2: phi^c = gamma mu^c (minus theta ln rho^c for "nid") from the
@@ -245,56 +348,192 @@ __device__ __forceinline__ bool mu_node(const R (&r)[N], const R (&lin)[N], cons
                                         : 0.0);
             phi[c] = ph;
         }
-    } else if constexpr (MU == MU_F32) {
-        float eta = 1.0f, rt = 0.0f;
-#pragma unroll
-        for (int c = 0; c < N; ++c) {
-            eta = __fmaf_rn(-P.b_hi[c], (float)r[c], eta);
-            rt += (float)r[c];
+    } else if constexpr (N == 2) {  // MU_DF / MU_F32: both components in one lane pair
+        const float2 r2 = make_float2(r[0], r[1]), l2 = make_float2(lin[0], lin[1]);
+        if constexpr (MU == MU_DF) {
+            DF<float2> ph;
+            ok = mu_pair_df<FORCE>(r2, l2, P, reinterpret_cast<const float4 *>(s_tbl), ph);
+            phi[0] = df{ph.hi.x, ph.lo.x};
+            phi[1] = df{ph.hi.y, ph.lo.y};
+        } else {
+            float2 ph;
+            ok = mu_pair_f32<FORCE>(r2, l2, P, ph);
+            phi[0] = ph.x;
+            phi[1] = ph.y;
         }
+    } else if constexpr (MU == MU_F32) {
+        float eta = 1.0f, rt = r[0];
+#pragma unroll
+        for (int c = 0; c < N; ++c) eta = __fmaf_rn(-P.b_hi[c], r[c], eta);
+#pragma unroll
+        for (int c = 1; c < N; ++c) rt = __fadd_rn(rt, r[c]);
         ok = ok && eta > 0.0f;
         const float ieta = 1.0f / eta;
+        const float rte = __fmul_rn(rt, ieta);
 #pragma unroll
-        for (int c = 0; c < N; ++c) {
-            const float m = logf((float)r[c] * ieta) + P.b_hi[c] * rt * ieta;
-            float ph = P.gkT_hi * m - P.gamma_hi * (float)lin[c];
-            if constexpr (FORCE == 1) ph -= (1.0f / 3.0f) * logf((float)r[c]);
-            phi[c] = ph;
-        }
-    } else {  // MU_DF
+        for (int c = 0; c < N; ++c) phi[c] = mu_f32_lanes<float, FORCE>(r[c], lin[c], P.b_hi[c], ieta, rte, P);
+    } else {  // MU_DF, one component lane at a time
         df eta = {1.0f, 0.0f};
 #pragma unroll
-        for (int c = 0; c < N; ++c) eta = df_add(eta, df_neg(df_mul_f({P.b_hi[c], P.b_lo[c]}, r[c])));
+        for (int c = 0; c < N; ++c) eta = df_add(eta, df_neg(df_mul_f(df{P.b_hi[c], P.b_lo[c]}, r[c])));
         // total density: the sum of the first two FP32 densities is exact as a pair
         df rt = N == 1 ? df{r[0], 0.0f} : df_two_sum(r[0], r[N > 1 ? 1 : 0]);
 #pragma unroll
-        for (int c = 2; c < N; ++c) rt = df_add(rt, {r[c], 0.0f});
+        for (int c = 2; c < N; ++c) rt = df_add(rt, df{r[c], 0.0f});
         ok = ok && eta.hi > 0.0f;
         const df ieta = df_recip(eta);
         const df rte = df_mul(rt, ieta);
 #pragma unroll
-        for (int c = 0; c < N; ++c) {
-            df lg = ok ? df_log(df_mul_f(ieta, r[c]), s_tbl, s_tbl + LOG_TBL, s_tbl + 2 * LOG_TBL, P.tbl->ln2_hi_f,
-                                P.tbl->ln2_lo_f)
-                       : df{0.0f, 0.0f};
-            df m = df_add(lg, df_mul(rte, {P.b_hi[c], P.b_lo[c]}));
-            df ph = df_add(df_mul(m, {P.gkT_hi, P.gkT_lo}), df_neg(df_mul_f({P.gamma_hi, P.gamma_lo}, lin[c])));
-            if constexpr (FORCE == 1) {
-                df lr = ok ? df_log({r[c], 0.0f}, s_tbl, s_tbl + LOG_TBL, s_tbl + 2 * LOG_TBL, P.tbl->ln2_hi_f,
-                                    P.tbl->ln2_lo_f)
-                           : df{0.0f, 0.0f};
-                ph = df_add(ph, df_neg(df_mul_f(lr, 1.0f / 3.0f)));
-            }
-            phi[c] = ph;
-        }
+        for (int c = 0; c < N; ++c)
+            phi[c] = mu_df_lanes<float, FORCE>(r[c], lin[c], df{P.b_hi[c], P.b_lo[c]}, ieta, rte, ok, P,
+                                               reinterpret_cast<const float4 *>(s_tbl));
     }
     return ok;
 }
 
-// One node of phase 3: from rho, Lap rho, D phi, D rho (log force) and the bare momenta,
-// the total gain G (mean field + implicit friction), then Psi, the forcing populations
-// and the BGK collision.  g holds the node's stored populations (deviations); post
-// receives the post-collision deviations in the same order.
+// ---------------------------------------------------------------------------
+// collision (Sec. III): per component lane, then the friction across components
+// ---------------------------------------------------------------------------
+// G^mu (Eq. forceMuLog: -rho D phi + theta D rho; Eq. forceMuId: -rho D phi), 1/rho, u = j/rho
+template <int FORCE, class V>
+__device__ __forceinline__ void gain_lane(V rho, V gpx, V gpy, V grx, V gry, V jx, V jy, V &Gx, V &Gy, V &ir, V &ux,
+                                          V &uy) {
+    if constexpr (FORCE == 0) {
+        Gx = v_fma(v_neg(rho), gpx, v_mul(grx, vc<V>(1.0 / 3.0)));
+        Gy = v_fma(v_neg(rho), gpy, v_mul(gry, vc<V>(1.0 / 3.0)));
+    } else {
+        Gx = v_mul(v_neg(rho), gpx);
+        Gy = v_mul(v_neg(rho), gpy);
+    }
+    ir = v_rcp(rho);
+    ux = v_mul(jx, ir);
+    uy = v_mul(jy, ir);
+}
+
+// cx a + cy b for a lattice direction (cx, cy in {-1, 0, 1}), exact
+template <int CX, int CY, class V>
+__device__ __forceinline__ V dir_dot(V a, V b) {
+    if constexpr (CY == 0) return CX == 1 ? a : v_neg(a);
+    else if constexpr (CX == 0) return CY == 1 ? b : v_neg(b);
+    else if constexpr (CX == CY) return CX == 1 ? v_add(a, b) : v_neg(v_add(a, b));
+    else return CX == 1 ? v_sub(a, b) : v_sub(b, a);
+}
+
+// One opposite pair (i, ip = -i) of the BGK collision with forcing.  With
+// A = w (drho + rho (4.5 (v.u)^2 - 1.5 u^2)), B = 3 w rho v.u, C = 4.5 w S:(vv - theta I),
+// D = 3 w v.G:  f^eq - w rho_ref = A +- B and F = C +- D (Eqs. feq, forcing terms);
+// post = (1 - omega) g + omega (f^eq - w rho_ref) + F.
+template <int LAT, int I, class V>
+__device__ __forceinline__ void bgk_pair(V r, V drho, V u, V v, V gx, V gy, V m15, V Sxx, V Syy, V Sxy, V omega,
+                                         V omc, V gi, V gip, V &pi, V &pip) {
+    using L = Lat<LAT>;
+    constexpr int CX = L::vx(I), CY = L::vy(I);
+    constexpr double W = L::w(I);
+    const V vu = dir_dot<CX, CY>(u, v);
+    const V vG = dir_dot<CX, CY>(gx, gy);
+    const V t = v_fma(vu, v_mul(vu, vc<V>(4.5)), m15);
+    const V A = v_fma(v_mul(r, vc<V>(W)), t, v_mul(drho, vc<V>(W)));
+    const V B = v_mul(vu, v_mul(r, vc<V>(3.0 * W)));
+    V C = v_mul(Sxx, vc<V>(4.5 * W * (CX * CX - 1.0 / 3.0)));
+    if constexpr (LAT == 2) {
+        C = v_fma(Syy, vc<V>(4.5 * W * (CY * CY - 1.0 / 3.0)), C);
+        if constexpr (CX * CY != 0) C = v_fma(Sxy, vc<V>(9.0 * W * CX * CY), C);
+    }
+    const V D = v_mul(vG, vc<V>(3.0 * W));
+    pi = v_fma(omc, gi, v_fma(omega, v_add(A, B), v_add(C, D)));
+    pip = v_fma(omc, gip, v_fma(omega, v_sub(A, B), v_sub(C, D)));
+}
+
+// BGK collision with forcing of one component lane.  The second forcing moment is
+// S = G u + u G - Psi, -Psi = cg G G / rho + cl Lap rho I (Eq. forceCorrectionsPsi, sigma = -1).
+// The moving populations come first; the rest population takes what is left of the
+// node's pre-collision mass (sum f^eq = rho and sum F = 0 make this the same value in
+// exact arithmetic), so mass is conserved up to the rounding of two sums.
+template <int LAT, class V>
+__device__ __forceinline__ void bgk_lane(V r, V u, V v, V gx, V gy, V lapc, V ir, V rref, V omega, V omc, V cg,
+                                         V cl, const V (&g)[Lat<LAT>::Q], V (&post)[Lat<LAT>::Q]) {
+    constexpr int Q = Lat<LAT>::Q;
+    const V cgi = v_mul(cg, ir);
+    const V cll = v_mul(cl, lapc);
+    const V Sxx = v_fma(gx, v_fma(gx, cgi, v_add(u, u)), cll);
+    V Syy = Sxx, Sxy = Sxx, usq;
+    if constexpr (LAT == 2) {
+        Syy = v_fma(gy, v_fma(gy, cgi, v_add(v, v)), cll);
+        Sxy = v_fma(gx, v_fma(gy, cgi, v), v_mul(u, gy));
+        usq = v_fma(u, u, v_mul(v, v));
+    } else {
+        usq = v_mul(u, u);
+    }
+    const V m15 = v_mul(usq, vc<V>(-1.5));
+    const V drho = v_sub(r, rref);
+    V moved;
+    if constexpr (LAT == 1) {
+        bgk_pair<1, 1>(r, drho, u, v, gx, gy, m15, Sxx, Syy, Sxy, omega, omc, g[1], g[2], post[1], post[2]);
+        moved = v_add(post[1], post[2]);
+    } else {
+        // pairs E/W, N/S, NE/SW, NW/SE
+        bgk_pair<2, 1>(r, drho, u, v, gx, gy, m15, Sxx, Syy, Sxy, omega, omc, g[1], g[3], post[1], post[3]);
+        bgk_pair<2, 2>(r, drho, u, v, gx, gy, m15, Sxx, Syy, Sxy, omega, omc, g[2], g[4], post[2], post[4]);
+        bgk_pair<2, 5>(r, drho, u, v, gx, gy, m15, Sxx, Syy, Sxy, omega, omc, g[5], g[7], post[5], post[7]);
+        bgk_pair<2, 6>(r, drho, u, v, gx, gy, m15, Sxx, Syy, Sxy, omega, omc, g[6], g[8], post[6], post[8]);
+        moved = v_add(post[1], post[3]);
+        moved = v_add(moved, v_add(post[2], post[4]));
+        moved = v_add(moved, v_add(post[5], post[7]));
+        moved = v_add(moved, v_add(post[6], post[8]));
+    }
+    V before = g[0];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) before = v_add(before, g[i]);
+    post[0] = v_sub(before, moved);
+}
+
+// Friction of two components with the implicit u-hat: (D + L/2) h = -L u0, G^f = D h per
+// direction (Eq. forceFriction).  L is rank one and the friction conserves momentum
+// (rho^1 h^1 = -rho^2 h^2), which leaves one unknown:
+//   G^{f,1} = -k (u0^1 - u0^2) = -G^{f,2},  k = [lambda / (1 + lambda/2)] rho^1 rho^2 / (rho^1 + rho^2),
+// u0^c = u^c + G^c / (2 rho^c) -- the system's exact solution.
+template <class T>
+__device__ __forceinline__ T friction_k(T r0, T r1, T lam_fr) {
+    return v_mul(v_mul(v_mul(lam_fr, r0), r1), v_rcp(v_add(r0, r1)));
+}
+
+// both components in one lane pair (x: component 1, y: component 2)
+__device__ __forceinline__ float2 friction_pair(float k, float2 G, float2 u, float2 ir) {
+    const float2 t = v_fma(G, v_mul(ir, vc<float2>(0.5)), u);
+    const float d = __fsub_rn(t.x, t.y);
+    return v_add(G, make_float2(__fmul_rn(-k, d), __fmul_rn(k, d)));
+}
+
+// one component per lane
+template <class T>
+__device__ __forceinline__ void friction_two(T k, T (&G)[2], const T (&u)[2], const T (&ir)[2]) {
+    const T t0 = v_fma(G[0], v_mul(ir[0], vc<T>(0.5)), u[0]);
+    const T t1 = v_fma(G[1], v_mul(ir[1], vc<T>(0.5)), u[1]);
+    const T d = v_sub(t0, t1);
+    G[0] = v_add(G[0], v_mul(-k, d));
+    G[1] = v_add(G[1], v_mul(k, d));
+}
+
+// One node of phase 3 for two components in one lane pair: from rho, Lap rho, D phi,
+// D rho ("log" force) and the bare momenta, the total gain G (mean field + implicit
+// friction), then Psi, the forcing populations and the BGK collision.  g holds the
+// node's stored populations (deviations); post receives the post-collision deviations.
+template <int LAT, int FORCE>
+__device__ __forceinline__ void collide_pair(float2 rho, float2 lap, float2 gpx, float2 gpy, float2 grx, float2 gry,
+                                             float2 jx, float2 jy, const DevParams &P,
+                                             const float2 (&g)[Lat<LAT>::Q], float2 (&post)[Lat<LAT>::Q]) {
+    float2 Gx, Gy, ir, ux, uy;
+    gain_lane<FORCE>(rho, gpx, gpy, grx, gry, jx, jy, Gx, Gy, ir, ux, uy);
+    const float k = friction_k(rho.x, rho.y, P.lam_fr_f);
+    Gx = friction_pair(k, Gx, ux, ir);
+    if constexpr (LAT == 2) Gy = friction_pair(k, Gy, uy, ir);
+    bgk_lane<LAT, float2>(rho, ux, uy, Gx, Gy, lap, ir, make_float2(P.rho_ref_f[0], P.rho_ref_f[1]),
+                          make_float2(P.omega_f, P.omega_f), make_float2(P.omc_f, P.omc_f),
+                          make_float2(P.psi_g_f, P.psi_g_f), make_float2(P.psi_l_f, P.psi_l_f), g, post);
+}
+
+// One node of phase 3, N components (arrays over c); two FP32 components go through the
+// lane-pair form above, with bitwise the same result as one component at a time.
 template <int LAT, int N, class R, int FORCE>
 __device__ __forceinline__ void collide_node(const R (&rho)[N], const R (&lap)[N], const R (&gpx)[N],
                                              const R (&gpy)[N], const R (&grx)[N], const R (&gry)[N],
@@ -302,140 +541,263 @@ __device__ __forceinline__ void collide_node(const R (&rho)[N], const R (&lap)[N
                                              const R (&g)[N][Lat<LAT>::Q], R (&post)[N][Lat<LAT>::Q]) {
     using L = Lat<LAT>;
     constexpr int Q = L::Q;
-    R ux[N], uy[N], Gx[N], Gy[N];
+    if constexpr (N == 2 && sizeof(R) == 4) {
+        float2 g2[Q], p2[Q];
 #pragma unroll
-    for (int c = 0; c < N; ++c) {
-        if constexpr (FORCE == 0) {
-            Gx[c] = -rho[c] * gpx[c] + (R)(1.0 / 3.0) * grx[c];
-            Gy[c] = -rho[c] * gpy[c] + (R)(1.0 / 3.0) * gry[c];
-        } else {
-            Gx[c] = -rho[c] * gpx[c];
-            Gy[c] = -rho[c] * gpy[c];
+        for (int i = 0; i < Q; ++i) g2[i] = make_float2(g[0][i], g[1][i]);
+        collide_pair<LAT, FORCE>(make_float2(rho[0], rho[1]), make_float2(lap[0], lap[1]),
+                                 make_float2(gpx[0], gpx[1]), make_float2(gpy[0], gpy[1]),
+                                 make_float2(grx[0], grx[1]), make_float2(gry[0], gry[1]),
+                                 make_float2(jx[0], jx[1]), make_float2(jy[0], jy[1]), P, g2, p2);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            post[0][i] = p2[i].x;
+            post[1][i] = p2[i].y;
         }
-        const R ir = rcp(rho[c]);
-        ux[c] = jx[c] * ir;
-        uy[c] = jy[c] * ir;
-    }
-
-    // friction with the implicit u-hat: (D + L/2) h = -L u0, G^f = D h  (per direction).
-    // Two components: L is rank one and the friction conserves momentum (rho^1 h^1 =
-    // -rho^2 h^2), which leaves one unknown: G^{f,1} = -lambda m (u0^1 - u0^2) / (1 + lambda/2)
-    // = -G^{f,2}, m = rho^1 rho^2 / (rho^1 + rho^2) -- the system's exact solution.
-    if constexpr (N == 2) {
-        const R lam = pv<R>(P.lam[1], P.lam_f[1]);
-        const R k = lam * rho[0] * rho[1] * rcp(rho[0] + rho[1]) * rcp((R)1 + (R)0.5 * lam);
-        const R h0 = (R)0.5 * rcp(rho[0]), h1 = (R)0.5 * rcp(rho[1]);
-        const R fx = -k * ((ux[0] + Gx[0] * h0) - (ux[1] + Gx[1] * h1));
-        Gx[0] += fx;
-        Gx[1] -= fx;
-        if constexpr (L::D == 2) {
-            const R fy = -k * ((uy[0] + Gy[0] * h0) - (uy[1] + Gy[1] * h1));
-            Gy[0] += fy;
-            Gy[1] -= fy;
+        return;
+    } else {
+        R ux[N], uy[N], Gx[N], Gy[N], ir[N];
+#pragma unroll
+        for (int c = 0; c < N; ++c) gain_lane<FORCE>(rho[c], gpx[c], gpy[c], grx[c], gry[c], jx[c], jy[c], Gx[c],
+                                                     Gy[c], ir[c], ux[c], uy[c]);
+        if constexpr (N == 2) {
+            const R k = friction_k(rho[0], rho[1], pv<R>(P.lam_fr, P.lam_fr_f));
+            friction_two(k, Gx, ux, ir);
+            if constexpr (L::D == 2) friction_two(k, Gy, uy, ir);
+        } else if constexpr (N > 2) {
+            R W[N][N];
+#pragma unroll
+            for (int c = 0; c < N; ++c)
+#pragma unroll
+                for (int cc = 0; cc < N; ++cc)
+                    W[c][cc] = (c == cc) ? (R)0
+                                         : pv<R>(P.lam[c * 4 + cc], P.lam_f[c * 4 + cc]) * rho[c] * rho[cc] *
+                                               rcp(rho[c] + rho[cc]);
+#pragma unroll
+            for (int d = 0; d < L::D; ++d) {
+                R u0[N], M[N][N], h[N];
+#pragma unroll
+                for (int c = 0; c < N; ++c) {
+                    R uu = d == 0 ? ux[c] : uy[c];
+                    R gg = d == 0 ? Gx[c] : Gy[c];
+                    u0[c] = uu + (R)0.5 * gg * rcp(rho[c]);
+                }
+#pragma unroll
+                for (int c = 0; c < N; ++c) {
+                    R diag = rho[c], rhs = (R)0;
+#pragma unroll
+                    for (int cc = 0; cc < N; ++cc) {
+                        M[c][cc] = (R)(-0.5) * W[c][cc];
+                        diag += (R)0.5 * W[c][cc];
+                        rhs -= W[c][cc] * (u0[c] - u0[cc]);
+                    }
+                    M[c][c] = diag;
+                    h[c] = rhs;
+                }
+                // symmetric positive definite: elimination without pivoting
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    R inv = rcp(M[k][k]);
+#pragma unroll
+                    for (int r2 = k + 1; r2 < N; ++r2) {
+                        R m = M[r2][k] * inv;
+#pragma unroll
+                        for (int c2 = k + 1; c2 < N; ++c2) M[r2][c2] -= m * M[k][c2];
+                        h[r2] -= m * h[k];
+                    }
+                }
+#pragma unroll
+                for (int k = N - 1; k >= 0; --k) {
+                    R sacc = h[k];
+#pragma unroll
+                    for (int c2 = k + 1; c2 < N; ++c2) sacc -= M[k][c2] * h[c2];
+                    h[k] = sacc * rcp(M[k][k]);
+                }
+#pragma unroll
+                for (int c = 0; c < N; ++c) {
+                    if (d == 0) Gx[c] += rho[c] * h[c];
+                    else Gy[c] += rho[c] * h[c];
+                }
+            }
         }
-    } else if constexpr (N > 2) {
-        R W[N][N];
+        const R omega = pv<R>(P.omega, P.omega_f), omc = pv<R>(P.omc, P.omc_f);
+        const R cg = pv<R>(P.psi_g, P.psi_g_f), cl = pv<R>(P.psi_l, P.psi_l_f);
 #pragma unroll
         for (int c = 0; c < N; ++c)
-#pragma unroll
-            for (int cc = 0; cc < N; ++cc)
-                W[c][cc] = (c == cc) ? (R)0
-                                     : pv<R>(P.lam[c * 4 + cc], P.lam_f[c * 4 + cc]) * rho[c] * rho[cc] *
-                                           rcp(rho[c] + rho[cc]);
-#pragma unroll
-        for (int d = 0; d < L::D; ++d) {
-            R u0[N], M[N][N], h[N];
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-                R uu = d == 0 ? ux[c] : uy[c];
-                R gg = d == 0 ? Gx[c] : Gy[c];
-                u0[c] = uu + (R)0.5 * gg * rcp(rho[c]);
-            }
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-                R diag = rho[c], rhs = (R)0;
-#pragma unroll
-                for (int cc = 0; cc < N; ++cc) {
-                    M[c][cc] = (R)(-0.5) * W[c][cc];
-                    diag += (R)0.5 * W[c][cc];
-                    rhs -= W[c][cc] * (u0[c] - u0[cc]);
-                }
-                M[c][c] = diag;
-                h[c] = rhs;
-            }
-            // symmetric positive definite: elimination without pivoting
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-                R inv = rcp(M[k][k]);
-#pragma unroll
-                for (int r2 = k + 1; r2 < N; ++r2) {
-                    R m = M[r2][k] * inv;
-#pragma unroll
-                    for (int c2 = k + 1; c2 < N; ++c2) M[r2][c2] -= m * M[k][c2];
-                    h[r2] -= m * h[k];
-                }
-            }
-#pragma unroll
-            for (int k = N - 1; k >= 0; --k) {
-                R sacc = h[k];
-#pragma unroll
-                for (int c2 = k + 1; c2 < N; ++c2) sacc -= M[k][c2] * h[c2];
-                h[k] = sacc * rcp(M[k][k]);
-            }
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-                if (d == 0) Gx[c] += rho[c] * h[c];
-                else Gy[c] += rho[c] * h[c];
+            bgk_lane<LAT, R>(rho[c], ux[c], uy[c], Gx[c], Gy[c], lap[c], ir[c], pv<R>(P.rho_ref[c], P.rho_ref_f[c]),
+                             omega, omc, cg, cl, g[c], post[c]);
+    }
+}
+
+// Tile geometry of the fused step: densities on the tile plus a 2-node ring, mu on the
+// tile plus a 1-node ring; the ring of the density array in one flat index k.
+template <int LAT, int TX, int TY>
+struct TileGeom {
+    static constexpr int HY = Lat<LAT>::HY;
+    static constexpr int EX = TX + 4, EY = TY + 4 * HY;  // densities: tile + 2 ring
+    static constexpr int MX = TX + 2, MY = TY + 2 * HY;  // mu: tile + 1 ring
+    static constexpr int NT = TX * TY;
+    static constexpr int RING = EX * EY - TX * TY;
+    __device__ static __forceinline__ void ring_node(int k, int &ex, int &ey) {
+        if constexpr (LAT == 1) {
+            ey = 0;
+            ex = k < 2 ? k : EX - 4 + k;
+        } else {
+            if (k < 2 * EX) {
+                ey = k / EX;
+                ex = k - ey * EX;
+            } else if (k < 4 * EX) {
+                int kk = k - 2 * EX;
+                ey = EY - 2 + kk / EX;
+                ex = kk % EX;
+            } else {
+                int kk = k - 4 * EX;
+                ey = 2 + (kk >> 2);
+                int col = kk & 3;
+                ex = col < 2 ? col : EX - 4 + col;
             }
         }
     }
+};
 
-    const R omega = pv<R>(P.omega, P.omega_f), cg = pv<R>(P.psi_g, P.psi_g_f), cl = pv<R>(P.psi_l, P.psi_l_f);
+// The fused step, two FP32 components in lane pairs: every per-node quantity of the two
+// components lives in one register pair (densities, momenta, mu, forces, populations) and
+// is computed by the packed FP32x2 instructions; shared memory holds the pairs
+// interleaved, so one 8-byte (16-byte for double-float mu) access moves both components.
+// Same arithmetic as the general step_tile below, bitwise.
+template <int LAT, int TX, int TY, int FORCE, int MU>
+__device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, float *__restrict__ fout,
+                                               const DevParams &P, int x0, int y0) {
+    using L = Lat<LAT>;
+    using G = TileGeom<LAT, TX, TY>;
+    constexpr int Q = L::Q, HY = G::HY, EX = G::EX, MX = G::MX, MY = G::MY, NT = G::NT;
+    static_assert(MU == MU_DF || MU == MU_F32, "lane pairs need an FP32-class mu");
+    using PT = typename std::conditional<MU == MU_DF, float4, float2>::type;  // phi pair: (hi, hi, lo, lo) / (x, y)
+
+    // the node's own populations wait in shared memory between phases 1 and 3 (tiles of up
+    // to 256 threads), else in registers
+    constexpr bool STAGE = NT <= 256;
+    __shared__ float2 s_g[STAGE ? Q : 1][STAGE ? NT : 1];
+    float2 gk[STAGE ? 1 : Q];
+    __shared__ float2 s_rho[G::EY * EX];
+    __shared__ PT s_phi[MY * MX];
+    __shared__ __align__(16) float s_tbl[TblWords<MU>::value];
+
+    const int nx = P.nx, ny = P.ny;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = tx + TX * ty;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool inside = x < nx && y < ny;
+    load_tables<MU>(s_tbl, P, tid, NT);
+    const size_t plane = (size_t)nx * (size_t)ny;
+    const size_t cq = (size_t)Q * plane;  // component stride
+    const bool small = nx <= TX + 1 || (LAT == 2 && ny <= TY + 1);
+    const float2 rref = make_float2(P.rho_ref_f[0], P.rho_ref_f[1]);
+
+    // ---- phase 1a: own node -> shared (populations, densities) ------------------
+    float2 jx, jy;
+    {
+        const int gx = small ? wrap(x, nx) : wrap1(x, nx);
+        const int gy = LAT == 1 ? 0 : (small ? wrap(y, ny) : wrap1(y, ny));
+        const float *src = fin + (size_t)gy * nx + gx;
+        float2 gv[Q], acc;
 #pragma unroll
-    for (int c = 0; c < N; ++c) {
-        const R r = rho[c], u = ux[c], v = uy[c], gx = Gx[c], gy = Gy[c];
-        const R ir = rcp(r);
-        // second forcing moment S = G u + u G - Psi, -Psi = cg G G / rho + cl Lap rho I
-        const R Sxx = (R)2 * gx * u + cg * gx * gx * ir + cl * lap[c];
-        const R Syy = (R)2 * gy * v + cg * gy * gy * ir + cl * lap[c];
-        const R Sxy = gx * v + u * gy + cg * gx * gy * ir;
-        const R usq = u * u + v * v;
-        const R drho = r - pv<R>(P.rho_ref[c], P.rho_ref_f[c]);
-        // Directions come in opposite pairs (i, i'): v.u, v.G flip sign, S:(vv - theta I)
-        // does not.  With A = w (drho + rho (4.5 (v.u)^2 - 1.5 u^2)), B = 3 w rho v.u,
-        // C = 4.5 w S:(vv - theta I), D = 3 w v.G:  f^eq - w rho_ref = A +- B, F = C +- D.
-        // The moving populations are computed first; the rest population takes what is
-        // left of the node's pre-collision mass (sum f^eq = rho, sum F = 0 make this the
-        // same value in exact arithmetic), so mass is conserved up to the rounding of
-        // two sums instead of drifting by (sum of the rounded weights - 1) every step.
-        const R third = (R)(1.0 / 3.0);
-        R moved = (R)0;
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const int cx = L::vx(i), cy = L::vy(i);
-            // handle each pair once, from its member with the smaller index
-            int ip = 0;
-#pragma unroll
-            for (int k = 1; k < Q; ++k)
-                if (L::vx(k) == -cx && L::vy(k) == -cy) ip = k;
-            if (ip < i) continue;
-            const R wi = (R)L::w(i);
-            const R vu = (R)cx * u + (R)cy * v;
-            const R vG = (R)cx * gx + (R)cy * gy;
-            R SQ = Sxx * ((R)(cx * cx) - third);
-            if constexpr (LAT == 2) SQ += Syy * ((R)(cy * cy) - third) + (R)2 * Sxy * (R)(cx * cy);
-            const R A = wi * (drho + r * ((R)4.5 * vu * vu - (R)1.5 * usq));
-            const R B = (R)3 * wi * r * vu;
-            const R C = (R)4.5 * wi * SQ;
-            const R D = (R)3 * wi * vG;
-            post[c][i] = g[c][i] + omega * (A + B - g[c][i]) + (C + D);
-            post[c][ip] = g[c][ip] + omega * (A - B - g[c][ip]) + (C - D);
-            moved += post[c][i] + post[c][ip];
+        for (int i = 0; i < Q; ++i) {
+            gv[i] = make_float2(src[(size_t)i * plane], src[cq + (size_t)i * plane]);
+            if constexpr (STAGE) s_g[i][tid] = gv[i];
+            else gk[i] = gv[i];
         }
-        R before = (R)0;
+        moments_lane<LAT>(gv, acc, jx, jy);
+        s_rho[(ty + 2 * HY) * EX + tx + 2] = v_add(rref, acc);
+    }
+    // ---- phase 1b: densities on the 2-node ring ---------------------------------
+    for (int k = tid; k < G::RING; k += NT) {
+        int ex, ey;
+        G::ring_node(k, ex, ey);
+        const int gx = small ? wrap(x0 + ex - 2, nx) : wrap1(x0 + ex - 2, nx);
+        const int gy = (LAT == 1) ? 0 : (small ? wrap(y0 + ey - 2, ny) : wrap1(y0 + ey - 2, ny));
+        const float *src = fin + (size_t)gy * nx + gx;
+        float2 acc = make_float2(src[0], src[cq]);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) before += g[c][i];
-        post[c][0] = before - moved;
+        for (int i = 1; i < Q; ++i) acc = v_add(acc, make_float2(src[(size_t)i * plane], src[cq + (size_t)i * plane]));
+        s_rho[ey * EX + ex] = v_add(rref, acc);
+    }
+    __syncthreads();
+
+    // ---- phase 2: phi on tile + 1 ring --------------------------------------------
+    unsigned bad = 0;
+    for (int k = tid; k < MX * MY; k += NT) {
+        const int mx = k % MX, my = k / MX;
+        const int e = (my + HY) * EX + mx + 1;
+        const float2 r = s_rho[e];
+        float2 lp;
+        if constexpr (LAT == 1) lp = lap_d1q3(r, s_rho[e + 1], s_rho[e - 1]);
+        else lp = lap_d2q9(nbr9(s_rho + e, EX));
+        const float2 lin = lin_pair(r, lp, P);
+        if constexpr (MU == MU_DF) {
+            DF<float2> ph;
+            if (!mu_pair_df<FORCE>(r, lin, P, reinterpret_cast<const float4 *>(s_tbl), ph)) bad = 1;
+            s_phi[k] = make_float4(ph.hi.x, ph.hi.y, ph.lo.x, ph.lo.y);
+        } else {
+            float2 ph;
+            if (!mu_pair_f32<FORCE>(r, lin, P, ph)) bad = 1;
+            s_phi[k] = ph;
+        }
+    }
+    __syncthreads();
+    if (bad) atomicOr(P.err, ERR_DOMAIN);
+    if (!inside) return;
+
+    // ---- phase 3: forces, collision, streaming ----------------------------------
+    const int e = (ty + 2 * HY) * EX + tx + 2;
+    const int m = (ty + HY) * MX + tx + 1;
+    const float2 rho = s_rho[e];
+    float2 lap, grx, gry, gpx, gpy;
+    auto phi_at = [&](int k) {
+        if constexpr (MU == MU_DF) {
+            const float4 t = s_phi[k];
+            return DF<float2>{make_float2(t.x, t.y), make_float2(t.z, t.w)};
+        } else {
+            return s_phi[k];
+        }
+    };
+    if constexpr (LAT == 1) {
+        lap = lap_d1q3(rho, s_rho[e + 1], s_rho[e - 1]);
+        grx = FORCE == 0 ? grad_d1q3(s_rho[e + 1], s_rho[e - 1]) : vc<float2>(0.0);
+        gry = vc<float2>(0.0);
+        gpx = v_mul(phi_diff2(phi_at(m + 1), phi_at(m - 1)), vc<float2>(0.5));
+        gpy = vc<float2>(0.0);
+    } else {
+        const Nbr9<float2> nb = nbr9(s_rho + e, EX);
+        lap = lap_d2q9(nb);
+        if constexpr (FORCE == 0) grad_d2q9(nb, grx, gry);
+        else grx = gry = vc<float2>(0.0);
+        grad_d2q9_diff(phi_diff2(phi_at(m + 1), phi_at(m - 1)), phi_diff2(phi_at(m + MX), phi_at(m - MX)),
+                       phi_diff2(phi_at(m + MX + 1), phi_at(m - MX - 1)),  // NE - SW
+                       phi_diff2(phi_at(m - MX + 1), phi_at(m + MX - 1)),  // SE - NW
+                       gpx, gpy);
+    }
+    float2 gr[Q], post[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if constexpr (STAGE) gr[i] = s_g[i][tid];
+        else gr[i] = gk[i];
+    }
+    collide_pair<LAT, FORCE>(rho, lap, gpx, gpy, grx, gry, jx, jy, P, gr, post);
+
+    // push streaming to the periodic neighbours
+    const int xe = small ? wrap(x + 1, nx) : (x + 1 == nx ? 0 : x + 1);
+    const int xw = small ? wrap(x - 1, nx) : (x == 0 ? nx - 1 : x - 1);
+    const int yn = LAT == 1 ? 0 : (small ? wrap(y + 1, ny) : (y + 1 == ny ? 0 : y + 1));
+    const int ys = LAT == 1 ? 0 : (small ? wrap(y - 1, ny) : (y == 0 ? ny - 1 : y - 1));
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = L::vx(i), cy = L::vy(i);
+        const int dx = cx == 1 ? xe : (cx == -1 ? xw : x);
+        const int dy = cy == 1 ? yn : (cy == -1 ? ys : y);
+        float *dst = fout + (size_t)i * plane + (size_t)dy * nx + dx;
+        dst[0] = post[i].x;
+        dst[cq] = post[i].y;
     }
 }
 
@@ -443,18 +805,19 @@ __device__ __forceinline__ void collide_node(const R (&rho)[N], const R (&lap)[N
 template <int LAT, int N, int TX, int TY, class S, class R, int FORCE, int MU>
 __device__ __forceinline__ void step_tile(const S *__restrict__ fin, S *__restrict__ fout, const DevParams &P,
                                           int x0, int y0) {
+    if constexpr (N == 2 && sizeof(S) == 4 && sizeof(R) == 4 && (MU == MU_DF || MU == MU_F32)) {
+        step_tile_pair<LAT, TX, TY, FORCE, MU>(fin, fout, P, x0, y0);
+    } else {
     using L = Lat<LAT>;
+    using G = TileGeom<LAT, TX, TY>;
     using MT = typename MuStore<MU>::T;
     constexpr int Q = L::Q;
     constexpr int HY = L::HY;
-    constexpr int EX = TX + 4, EY = TY + 4 * HY;  // densities: tile + 2 ring
-    constexpr int MX = TX + 2, MY = TY + 2 * HY;  // mu: tile + 1 ring
-    constexpr int NT = TX * TY;
-    constexpr int RING = EX * EY - TX * TY;
+    constexpr int EX = G::EX, EY = G::EY, MX = G::MX, MY = G::MY, NT = G::NT;
     // Between phase 1 and phase 3 the node's own populations wait in shared memory (FP32
-    // storage, up to two components, 256-thread tiles: this frees 18 registers for the mu
-    // phase and measured 3 % faster than holding them in registers), else in registers when
-    // they fit comfortably, else they are loaded again in phase 3.
+    // storage, up to two components, 256-thread tiles: this frees registers for the mu
+    // phase), else in registers when they fit comfortably, else they are loaded again in
+    // phase 3.
     constexpr bool STAGE = sizeof(S) == 4 && N <= 2 && NT <= 256;
     constexpr bool KEEP = !STAGE && sizeof(S) * N * Q <= 144;
     __shared__ S s_g[STAGE ? N * Q : 1][STAGE ? NT : 1];
@@ -484,54 +847,31 @@ __device__ __forceinline__ void step_tile(const S *__restrict__ fin, S *__restri
         const int ex = tx + 2, ey = ty + 2 * HY;
 #pragma unroll
         for (int c = 0; c < N; ++c) {
-            R acc = (R)0, ax = (R)0, ay = (R)0;
+            R gv[Q], acc;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 S v = src[(size_t)(c * Q + i) * plane];
                 if constexpr (KEEP) g[c][i] = v;
                 if constexpr (STAGE) s_g[c * Q + i][tid] = v;
-                R rv = (R)v;
-                acc += rv;
-                if (L::vx(i) == 1) ax += rv;
-                if (L::vx(i) == -1) ax -= rv;
-                if (L::vy(i) == 1) ay += rv;
-                if (L::vy(i) == -1) ay -= rv;
+                gv[i] = (R)v;
             }
-            s_rho[c][ey * EX + ex] = pv<R>(P.rho_ref[c], P.rho_ref_f[c]) + acc;
-            jx[c] = ax;
-            jy[c] = ay;
+            moments_lane<LAT>(gv, acc, jx[c], jy[c]);
+            s_rho[c][ey * EX + ex] = v_add(pv<R>(P.rho_ref[c], P.rho_ref_f[c]), acc);
         }
     }
     // ---- phase 1b: rho^c on the 2-node ring -----------------------------------
-    for (int k = tid; k < RING; k += NT) {
+    for (int k = tid; k < G::RING; k += NT) {
         int ex, ey;
-        if constexpr (LAT == 1) {
-            ey = 0;
-            ex = k < 2 ? k : EX - 4 + k;
-        } else {
-            if (k < 2 * EX) {
-                ey = k / EX;
-                ex = k - ey * EX;
-            } else if (k < 4 * EX) {
-                int kk = k - 2 * EX;
-                ey = EY - 2 + kk / EX;
-                ex = kk % EX;
-            } else {
-                int kk = k - 4 * EX;
-                ey = 2 + (kk >> 2);
-                int col = kk & 3;
-                ex = col < 2 ? col : EX - 4 + col;
-            }
-        }
+        G::ring_node(k, ex, ey);
         const int gx = small ? wrap(x0 + ex - 2, nx) : wrap1(x0 + ex - 2, nx);
         const int gy = (LAT == 1) ? 0 : (small ? wrap(y0 + ey - 2, ny) : wrap1(y0 + ey - 2, ny));
         const S *src = fin + (size_t)gy * nx + gx;
 #pragma unroll
         for (int c = 0; c < N; ++c) {
-            R acc = (R)0;
+            R acc = (R)src[(size_t)(c * Q) * plane];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) acc += (R)src[(size_t)(c * Q + i) * plane];
-            s_rho[c][ey * EX + ex] = pv<R>(P.rho_ref[c], P.rho_ref_f[c]) + acc;
+            for (int i = 1; i < Q; ++i) acc = v_add(acc, (R)src[(size_t)(c * Q + i) * plane]);
+            s_rho[c][ey * EX + ex] = v_add(pv<R>(P.rho_ref[c], P.rho_ref_f[c]), acc);
         }
     }
     __syncthreads();
@@ -541,20 +881,13 @@ __device__ __forceinline__ void step_tile(const S *__restrict__ fin, S *__restri
     for (int k = tid; k < MX * MY; k += NT) {
         const int mx = k % MX, my = k / MX;
         const int ex = mx + 1, ey = my + HY;
-        R r[N], lin[N];
+        R r[N], lp[N], lin[N];
 #pragma unroll
         for (int c = 0; c < N; ++c) {
             r[c] = s_rho[c][ey * EX + ex];
-            lin[c] = (R)0;
+            lp[c] = lap_at<LAT, R>(s_rho[c], ex, ey, EX);
         }
-#pragma unroll
-        for (int cc = 0; cc < N; ++cc) {
-            R lp = lap_at<LAT, R>(s_rho[cc], ex, ey, EX);
-#pragma unroll
-            for (int c = 0; c < N; ++c)
-                lin[c] += pv<R>(2.0 * P.a[c * 4 + cc], P.a2_f[c * 4 + cc]) * r[cc] +
-                          pv<R>(P.kappa[c * 4 + cc], P.kappa_f[c * 4 + cc]) * lp;
-        }
+        lin_node<N, R>(r, lp, P, lin);
         MT phi[N];
         if (!mu_node<N, R, FORCE, MU>(r, lin, P, s_tbl, phi)) bad = 1;
 #pragma unroll
@@ -601,6 +934,7 @@ __device__ __forceinline__ void step_tile(const S *__restrict__ fin, S *__restri
             const int dy = cy == 1 ? yn : (cy == -1 ? ys : y);
             fout[(size_t)(c * Q + i) * plane + (size_t)dy * nx + dx] = (S)post[c][i];
         }
+    }
 }
 
 // FP32 storage with up to two components: ask for five resident 256-thread CTAs per SM

@@ -28,6 +28,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "lb_lane.cuh"
+
 namespace lbvdw {
 
 constexpr int LOG_TBL = 128;  // sub-intervals of [1, 2)
@@ -35,8 +37,9 @@ constexpr int LOG_TBL = 128;  // sub-intervals of [1, 2)
 struct LogTables {
     // FP64 table: r_j = 1/c_j rounded to double, T_j = -ln(r_j) as hi + lo
     double r64[LOG_TBL], t64_hi[LOG_TBL], t64_lo[LOG_TBL];
-    // df table: r_j = 1/c_j rounded to float, T_j = -ln(r_j) as float hi + lo
-    float r32[LOG_TBL], t32_hi[LOG_TBL], t32_lo[LOG_TBL];
+    // df table: (r_j = 1/c_j rounded to float, T_j = -ln(r_j) as float hi + lo, 0): one
+    // 16-byte load per logarithm
+    float4 t32[LOG_TBL];
     // ln 2 = hi + lo: FP64 hi short enough that e * hi is exact (|e| < 2^10);
     // float pair = ln 2 rounded to float plus the rounded remainder
     double ln2_hi_d, ln2_lo_d;
@@ -70,46 +73,8 @@ __device__ __forceinline__ double log64_tbl(double x, const double *s_r, const d
 }
 
 // ------------------------------------------------------------------ double-float
-struct df {
-    float hi, lo;
-};
-
-__device__ __forceinline__ df df_quick(float a, float b) {  // |a| >= |b|
-    float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-
-__device__ __forceinline__ df df_two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    float bb = __fsub_rn(s, a);
-    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return {s, e};
-}
-
-__device__ __forceinline__ df df_two_prod(float a, float b) {
-    float p = __fmul_rn(a, b);
-    return {p, __fmaf_rn(a, b, -p)};
-}
-
-__device__ __forceinline__ df df_add(df a, df b) {
-    df s = df_two_sum(a.hi, b.hi);
-    float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
-    return df_quick(s.hi, lo);
-}
-
-__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
-
-__device__ __forceinline__ df df_mul(df a, df b) {
-    df p = df_two_prod(a.hi, b.hi);
-    float lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
-    return df_quick(p.hi, lo);
-}
-
-__device__ __forceinline__ df df_mul_f(df a, float b) {
-    df p = df_two_prod(a.hi, b);
-    float lo = __fmaf_rn(a.lo, b, p.lo);
-    return df_quick(p.hi, lo);
-}
+// The double-float operations on lanes are in lb_lane.cuh; df is one scalar lane.
+using df = DF<float>;
 
 __device__ __forceinline__ df df_from_double(double v) {
     float hi = __double2float_rn(v);
@@ -125,42 +90,67 @@ __device__ __forceinline__ df df_recip(df a) {
     float y = __frcp_rn(a.hi);
     // e = 1 - a*y in df, then y + y*e
     df ay = df_mul_f(a, y);
-    df e = df_add({1.0f, 0.0f}, df_neg(ay));
+    df e = df_add(df{1.0f, 0.0f}, df_neg(ay));
     df ye = df_two_prod(y, e.hi);
     ye.lo = __fmaf_rn(y, e.lo, ye.lo);
-    return df_add({y, 0.0f}, df_quick(ye.hi, ye.lo));
+    return df_add(df{y, 0.0f}, df_quick(ye.hi, ye.lo));
 }
 
-// natural log of a positive, normal df value
-__device__ __forceinline__ df df_log(df x, const float *s_r, const float *s_hi, const float *s_lo, float ln2_hi,
-                                     float ln2_lo) {
-    int bits = __float_as_int(x.hi);
-    int e = ((bits >> 23) & 0xff) - 127;
-    int j = (bits >> 16) & (LOG_TBL - 1);
+// The per-lane part of the table reduction: x_hi = 2^e m, j = top 7 bits of the mantissa;
+// returns the scale 2^-e, e and the table entry (r_j, T_j hi, T_j lo).
+struct LogRed {
+    float sc, e;
+    float4 t;
+};
+__device__ __forceinline__ LogRed log_reduce(float xh, const float4 *s_t) {
+    const int bits = __float_as_int(xh);
+    const int e = ((bits >> 23) & 0xff) - 127;
+    const int j = (bits >> 16) & (LOG_TBL - 1);
+    return {__int_as_float((127 - e) << 23), (float)e, s_t[j]};
+}
+
+__device__ __forceinline__ void log_lanes(float xh, const float4 *s_t, float &sc, float &e, float &r, float &thi,
+                                          float &tlo) {
+    const LogRed q = log_reduce(xh, s_t);
+    sc = q.sc, e = q.e, r = q.t.x, thi = q.t.y, tlo = q.t.z;
+}
+__device__ __forceinline__ void log_lanes(float2 xh, const float4 *s_t, float2 &sc, float2 &e, float2 &r, float2 &thi,
+                                          float2 &tlo) {
+    const LogRed a = log_reduce(xh.x, s_t), b = log_reduce(xh.y, s_t);
+    sc = make_float2(a.sc, b.sc), e = make_float2(a.e, b.e), r = make_float2(a.t.x, b.t.x);
+    thi = make_float2(a.t.y, b.t.y), tlo = make_float2(a.t.z, b.t.z);
+}
+
+// natural log of positive, normal df lanes.  s_t: the table (r_j, -ln r_j as hi + lo)
+// in shared memory; a non-positive or non-finite input gives a meaningless value (the
+// table index stays in range).
+template <class V>
+__device__ __forceinline__ DF<V> df_log(DF<V> x, const float4 *s_t, float ln2_hi, float ln2_lo) {
+    V sc, ef, rj, thi, tlo;
+    log_lanes(x.hi, s_t, sc, ef, rj, thi, tlo);
     // scale by 2^-e (exact for both parts)
-    float sc = __int_as_float((127 - e) << 23);
-    float mh = __fmul_rn(x.hi, sc), ml = __fmul_rn(x.lo, sc);
+    const V mh = v_mul(x.hi, sc), ml = v_mul(x.lo, sc);
     // t = m r_j in df; r = t - 1 (t.hi - 1 is exact: t.hi lies within 2^-7 of 1)
-    df t = df_two_prod(mh, s_r[j]);
-    t.lo = __fmaf_rn(ml, s_r[j], t.lo);
-    df r = df_two_sum(__fsub_rn(t.hi, 1.0f), t.lo);
+    DF<V> t = df_two_prod(mh, rj);
+    t.lo = v_fma(ml, rj, t.lo);
+    const DF<V> r = df_two_sum(v_sub(t.hi, vc<V>(1.0)), t.lo);
     // log1p(r) = r - r^2/2 + r^3 (1/3 - r/4 + r^2/5 - r^3/6), the tail in FP32
-    df r2 = df_two_prod(r.hi, r.hi);
-    r2.lo = __fmaf_rn(2.0f * r.hi, r.lo, r2.lo);
-    df half_r2 = {0.5f * r2.hi, 0.5f * r2.lo};
-    float rh = r.hi;
-    float q = __fmaf_rn(rh, -1.0f / 6.0f, 0.2f);
-    q = __fmaf_rn(rh, q, -0.25f);
-    q = __fmaf_rn(rh, q, 1.0f / 3.0f);
-    float tail = q * (rh * rh * rh);
+    DF<V> r2 = df_two_prod(r.hi, r.hi);
+    r2.lo = v_fma(v_add(r.hi, r.hi), r.lo, r2.lo);
+    const V h2hi = v_mul(r2.hi, vc<V>(0.5)), h2lo = v_mul(r2.lo, vc<V>(0.5));
+    const V rh = r.hi;
+    V q = v_fma(rh, vc<V>(-1.0 / 6.0), vc<V>(0.2));
+    q = v_fma(rh, q, vc<V>(-0.25));
+    q = v_fma(rh, q, vc<V>(1.0 / 3.0));
+    const V tail = v_mul(q, v_mul(v_mul(rh, rh), rh));
     // |r| > |r^2/2| > |tail|: the ordered (quick) sums are exact here
-    df l1p = df_quick(r.hi, -half_r2.hi);
-    l1p = df_quick(l1p.hi, __fadd_rn(l1p.lo, __fsub_rn(r.lo, half_r2.lo)));
-    l1p = df_quick(l1p.hi, __fadd_rn(l1p.lo, tail));
+    DF<V> l1p = df_quick(rh, v_neg(h2hi));
+    l1p = df_quick(l1p.hi, v_add(l1p.lo, v_sub(r.lo, h2lo)));
+    l1p = df_quick(l1p.hi, v_add(l1p.lo, tail));
     // e ln 2 + T_j: |e ln 2| >= ln 2 > |T_j| unless e = 0, when the quick sum is exact too
-    df eln2 = df_mul_f({ln2_hi, ln2_lo}, (float)e);
-    df et = df_quick(eln2.hi, s_hi[j]);
-    et = df_quick(et.hi, __fadd_rn(et.lo, __fadd_rn(eln2.lo, s_lo[j])));
+    const DF<V> eln2 = df_mul_f(df_splat(df{ln2_hi, ln2_lo}, ef), ef);
+    DF<V> et = df_quick(eln2.hi, thi);
+    et = df_quick(et.hi, v_add(et.lo, v_add(eln2.lo, tlo)));
     return df_add(et, l1p);
 }
 

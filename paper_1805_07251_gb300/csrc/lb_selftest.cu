@@ -18,8 +18,7 @@ __global__ void selftest_log_kernel(const double *x, long long n, const lbvdw::L
     if (k >= n) return;
     double v = x[k];
     o_tbl[k] = lbvdw::log64_tbl(v, tb->r64, tb->t64_hi, tb->t64_lo, tb->ln2_hi_d, tb->ln2_lo_d);
-    lbvdw::df d = lbvdw::df_log(lbvdw::df_from_double(v), tb->r32, tb->t32_hi, tb->t32_lo, tb->ln2_hi_f,
-                                tb->ln2_lo_f);
+    lbvdw::df d = lbvdw::df_log(lbvdw::df_from_double(v), tb->t32, tb->ln2_hi_f, tb->ln2_lo_f);
     o_df[k] = lbvdw::df_to_double(d);
     o_ref[k] = log(v);
 }

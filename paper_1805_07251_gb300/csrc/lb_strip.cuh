@@ -86,31 +86,29 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
 
 // ---------------------------------------------------------------------------
 // stencils on three row pointers (rows y-1, y, y+1 of a ring buffer); the same
-// arithmetic, in the same order, as grad_at / lap_at / grad_phi of lb_kernels.cuh
+// arithmetic as grad_at / lap_at / grad_phi of lb_kernels.cuh (lb_lane.cuh)
 // ---------------------------------------------------------------------------
 template <class T>
+__device__ __forceinline__ Nbr9<T> nbr_rows(const T *s, const T *m, const T *n, int x) {
+    return {m[x], m[x + 1], m[x - 1], n[x], s[x], n[x + 1], n[x - 1], s[x - 1], s[x + 1]};
+}
+
+template <class T>
 __device__ __forceinline__ T lap_rows(const T *s, const T *m, const T *n, int x) {
-    T axis = (m[x + 1] + m[x - 1]) + (n[x] + s[x]);
-    T diag = (n[x + 1] + n[x - 1]) + (s[x + 1] + s[x - 1]);
-    return axis * (T)(2.0 / 3.0) + diag * (T)(1.0 / 6.0) - m[x] * (T)(10.0 / 3.0);
+    return lap_d2q9(nbr_rows(s, m, n, x));
 }
 
 template <class T>
 __device__ __forceinline__ void grad_rows(const T *s, const T *m, const T *n, int x, T &gx, T &gy) {
-    T e = m[x + 1], wv = m[x - 1], nv = n[x], sv = s[x];
-    T ne = n[x + 1], nw = n[x - 1], sw = s[x - 1], se = s[x + 1];
-    gx = (e - wv) * (T)(1.0 / 3.0) + ((ne + se) - (nw + sw)) * (T)(1.0 / 12.0);
-    gy = (nv - sv) * (T)(1.0 / 3.0) + ((ne + nw) - (se + sw)) * (T)(1.0 / 12.0);
+    grad_d2q9(nbr_rows(s, m, n, x), gx, gy);
 }
 
 template <class R, class T>
 __device__ __forceinline__ void grad_phi_rows(const T *s, const T *m, const T *n, int x, R &gx, R &gy) {
-    R ew = phi_diff<R>(m[x + 1], m[x - 1]);
-    R ns = phi_diff<R>(n[x], s[x]);
-    R d1 = phi_diff<R>(n[x + 1], s[x - 1]);  // NE - SW
-    R d2 = phi_diff<R>(s[x + 1], n[x - 1]);  // SE - NW
-    gx = ew * (R)(1.0 / 3.0) + (d1 + d2) * (R)(1.0 / 12.0);
-    gy = ns * (R)(1.0 / 3.0) + (d1 - d2) * (R)(1.0 / 12.0);
+    grad_d2q9_diff(phi_diff<R>(m[x + 1], m[x - 1]), phi_diff<R>(n[x], s[x]),
+                   phi_diff<R>(n[x + 1], s[x - 1]),  // NE - SW
+                   phi_diff<R>(s[x + 1], n[x - 1]),  // SE - NW
+                   gx, gy);
 }
 
 // ---------------------------------------------------------------------------
@@ -183,10 +181,10 @@ __device__ __forceinline__ void strip_rho(const float *pop, R *s_rho, const DevP
     const int ring_row = yy & (RING - 1);
 #pragma unroll
     for (int c = 0; c < N; ++c) {
-        R acc = (R)0;
+        R acc = (R)src[(size_t)(c * Lay::Q) * TY * PW];
 #pragma unroll
-        for (int i = 0; i < Lay::Q; ++i) acc += (R)src[(size_t)(c * Lay::Q + i) * TY * PW];
-        s_rho[((size_t)c * RING + ring_row) * RW + cc] = pv<R>(P.rho_ref[c], P.rho_ref_f[c]) + acc;
+        for (int i = 1; i < Lay::Q; ++i) acc = v_add(acc, (R)src[(size_t)(c * Lay::Q + i) * TY * PW]);
+        s_rho[((size_t)c * RING + ring_row) * RW + cc] = v_add(pv<R>(P.rho_ref[c], P.rho_ref_f[c]), acc);
     }
 }
 
@@ -202,21 +200,14 @@ __device__ __forceinline__ bool strip_mu(const R *s_rho, typename MuStore<MU>::T
     const int cm = tid % MW, yy = yy0 + tid / MW;
     const int ex = cm + 1;  // rho ring column of this node
     const int rs = (yy - 1) & (RING - 1), rm = yy & (RING - 1), rn = (yy + 1) & (RING - 1);
-    R r[N], lin[N];
+    R r[N], lp[N], lin[N];
 #pragma unroll
     for (int c = 0; c < N; ++c) {
-        r[c] = s_rho[((size_t)c * RING + rm) * RW + ex];
-        lin[c] = (R)0;
+        const R *base = s_rho + (size_t)c * RING * RW;
+        r[c] = base[rm * RW + ex];
+        lp[c] = lap_rows<R>(base + rs * RW, base + rm * RW, base + rn * RW, ex);
     }
-#pragma unroll
-    for (int cc = 0; cc < N; ++cc) {
-        const R *base = s_rho + (size_t)cc * RING * RW;
-        R lp = lap_rows<R>(base + rs * RW, base + rm * RW, base + rn * RW, ex);
-#pragma unroll
-        for (int c = 0; c < N; ++c)
-            lin[c] += pv<R>(2.0 * P.a[c * 4 + cc], P.a2_f[c * 4 + cc]) * r[cc] +
-                      pv<R>(P.kappa[c * 4 + cc], P.kappa_f[c * 4 + cc]) * lp;
-    }
+    lin_node<N, R>(r, lp, P, lin);
     MT phi[N];
     const bool ok = mu_node<N, R, FORCE, MU>(r, lin, P, s_tbl, phi);
 #pragma unroll
@@ -301,18 +292,10 @@ __global__ void __launch_bounds__(StripLayout<N, TX, TY, MU>::NT, 2)
             R rho[N], lap[N], gpx[N], gpy[N], grx[N], gry[N], jx[N], jy[N], gr[N][Q], post[N][Q];
 #pragma unroll
             for (int c = 0; c < N; ++c) {
-                R ax = (R)0, ay = (R)0;
+                R acc;
 #pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    R rv = (R)src[(size_t)(c * Q + i) * TY * PW];
-                    gr[c][i] = rv;
-                    if (L::vx(i) == 1) ax += rv;
-                    if (L::vx(i) == -1) ax -= rv;
-                    if (L::vy(i) == 1) ay += rv;
-                    if (L::vy(i) == -1) ay -= rv;
-                }
-                jx[c] = ax;
-                jy[c] = ay;
+                for (int i = 0; i < Q; ++i) gr[c][i] = (R)src[(size_t)(c * Q + i) * TY * PW];
+                moments_lane<2>(gr[c], acc, jx[c], jy[c]);
                 const R *rb = s_rho + (size_t)c * RING * RW;
                 const int ex = col + 2;
                 rho[c] = rb[rm * RW + ex];
