@@ -211,8 +211,11 @@ void make_dev_params(const lb_params &p, DevParams &d, unsigned *err, const LogT
     d.err = err;
     d.tbl = tbl;
     d.gkT = p.gamma_mu * p.kT;
-    split_float(d.gkT, d.gkT_hi, d.gkT_lo);
-    split_float(p.gamma_mu, d.gamma_hi, d.gamma_lo);
+    d.ikT_f = (float)(1.0 / p.kT);
+    d.gkt3_f = (float)(d.gkT / 3.0);
+    d.gkt12_f = (float)(d.gkT / 12.0);
+    d.gkt2_f = (float)(d.gkT / 2.0);
+    split_float(1.0 / (3.0 * d.gkT), d.cnid_hi, d.cnid_lo);
     d.omega_f = (float)d.omega;
     d.psi_g_f = (float)d.psi_g;
     d.psi_l_f = (float)d.psi_l;

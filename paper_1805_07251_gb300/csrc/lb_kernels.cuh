@@ -38,8 +38,12 @@ struct DevParams {
     unsigned *err;      // error word (device)
     const LogTables *tbl;  // log tables (device)
     double gkT;         // gamma_mu * kT
-    float b_hi[4], b_lo[4];  // double-float copies of b, gamma kT and gamma
-    float gkT_hi, gkT_lo, gamma_hi, gamma_lo;
+    float b_hi[4], b_lo[4];  // double-float copies of b
+    // FP32-class mu paths store phi / (gamma kT) = mu / kT (- ln rho / (3 gamma kT) for
+    // "nid"); gamma kT then enters with the gradient weights
+    float ikT_f;                  // 1 / kT
+    float gkt3_f, gkt12_f, gkt2_f;  // gamma kT / 3, gamma kT / 12, gamma kT / 2
+    float cnid_hi, cnid_lo;       // 1 / (3 gamma kT) as a double-float
     // FP32 copies for the FP32 paths (no double->float conversion in the kernels)
     float a2_f[16], kappa_f[16], lam_f[16];  // 2 a, kappa, lambda
     float rho_ref_f[4], omega_f, psi_g_f, psi_l_f;
@@ -156,18 +160,35 @@ __device__ __forceinline__ float2 phi_diff2(DF<float2> a, DF<float2> b) {
     return v_add(v_sub(a.hi, b.hi), v_sub(a.lo, b.lo));
 }
 
-// D phi at (mx, my) of an MX-wide shared array, differences in the mu arithmetic
+// The weights of D phi: 1/3, 1/12 (D2Q9) and 1/2 (D1Q3) times the scale of the stored phi
+// (gamma kT for the FP32-class mu paths, which store phi / (gamma kT); 1 otherwise).
+template <class T> struct PhiScaled { static constexpr bool value = false; };
+template <> struct PhiScaled<df> { static constexpr bool value = true; };
+template <> struct PhiScaled<float> { static constexpr bool value = true; };
+
+template <class R, class T>
+__device__ __forceinline__ void phi_weights(const DevParams &P, R &c3, R &c12, R &c2) {
+    if constexpr (PhiScaled<T>::value) {
+        c3 = P.gkt3_f, c12 = P.gkt12_f, c2 = P.gkt2_f;
+    } else {
+        c3 = vc<R>(1.0 / 3.0), c12 = vc<R>(1.0 / 12.0), c2 = vc<R>(0.5);
+    }
+}
+
+// D (gamma mu) at (mx, my) of an MX-wide shared array of phi, differences in the mu arithmetic
 template <int LAT, class R, class T>
-__device__ __forceinline__ void grad_phi(const T *s, int mx, int my, int MXW, R &gx, R &gy) {
+__device__ __forceinline__ void grad_phi(const T *s, int mx, int my, int MXW, const DevParams &P, R &gx, R &gy) {
     const T *p = s + my * MXW + mx;
+    R c3, c12, c2;
+    phi_weights<R, T>(P, c3, c12, c2);
     if constexpr (LAT == 1) {
-        gx = v_mul(phi_diff<R>(p[1], p[-1]), vc<R>(0.5));
+        gx = v_mul(phi_diff<R>(p[1], p[-1]), c2);
         gy = vc<R>(0.0);
     } else {
         grad_d2q9_diff(phi_diff<R>(p[1], p[-1]), phi_diff<R>(p[MXW], p[-MXW]),
                        phi_diff<R>(p[MXW + 1], p[-MXW - 1]),  // NE - SW
                        phi_diff<R>(p[-MXW + 1], p[MXW - 1]),  // SE - NW
-                       gx, gy);
+                       c3, c12, gx, gy);
     }
 }
 
@@ -248,19 +269,20 @@ __device__ __forceinline__ float2 lin_pair(float2 r, float2 lp, const DevParams 
 __device__ __forceinline__ float v_log(float x) { return logf(x); }
 __device__ __forceinline__ float2 v_log(float2 x) { return make_float2(logf(x.x), logf(x.y)); }
 
+// phi^c / (gamma kT) = ln(rho^c / eta) + b^c rho / eta - lin^c / kT (minus ln rho^c / (3 gamma kT)
+// for "nid") of one component lane, from the node's 1/eta and rho/eta
 template <class V, int FORCE>
 __device__ __forceinline__ DF<V> mu_df_lanes(V r, V lin, DF<V> b, df ieta, df rte, bool ok, const DevParams &P,
                                              const float4 *s_t) {
     const V zero = vc<V>(0.0);
-    DF<V> lg = df_log(df_mul_f(df_splat(ieta, r), r), s_t, P.ln2_hi_f, P.ln2_lo_f);
+    DF<V> lg = df_log(df_mul_fu(df_splat(ieta, r), r), s_t, P.ln2_hi_f, P.ln2_lo_f);
     if (!ok) lg = DF<V>{zero, zero};
-    const DF<V> m = df_add(lg, df_mul(df_splat(rte, r), b));
-    DF<V> ph = df_add(df_mul(m, df_splat(df{P.gkT_hi, P.gkT_lo}, r)),
-                      df_neg(df_mul_f(df_splat(df{P.gamma_hi, P.gamma_lo}, r), lin)));
+    const DF<V> m = df_add(lg, df_mul_u(df_splat(rte, r), b));
+    DF<V> ph = df_add_f(m, v_mul(lin, vs(-P.ikT_f, r)));
     if constexpr (FORCE == 1) {
         DF<V> lr = df_log(DF<V>{r, zero}, s_t, P.ln2_hi_f, P.ln2_lo_f);
         if (!ok) lr = DF<V>{zero, zero};
-        ph = df_add(ph, df_neg(df_mul_f(lr, vc<V>(1.0 / 3.0))));
+        ph = df_add(ph, df_neg(df_mul_u(lr, df_splat(df{P.cnid_hi, P.cnid_lo}, r))));
     }
     return ph;
 }
@@ -268,9 +290,16 @@ __device__ __forceinline__ DF<V> mu_df_lanes(V r, V lin, DF<V> b, df ieta, df rt
 template <class V, int FORCE>
 __device__ __forceinline__ V mu_f32_lanes(V r, V lin, V b, float ieta, float rte, const DevParams &P) {
     const V lg = v_log(v_mul(r, vs(ieta, r)));
-    V ph = v_fma(vs(P.gkT_hi, r), v_fma(b, vs(rte, r), lg), v_mul(vs(-P.gamma_hi, r), lin));
-    if constexpr (FORCE == 1) ph = v_fma(vc<V>(-1.0 / 3.0), v_log(r), ph);
+    V ph = v_fma(lin, vs(-P.ikT_f, r), v_fma(b, vs(rte, r), lg));
+    if constexpr (FORCE == 1) ph = v_fma(v_log(r), vs(-P.cnid_hi, r), ph);
     return ph;
+}
+
+// eta = 1 - S from S = sum_c b^c rho^c (an unnormalised df): the quick sum is exact while
+// S.hi < 1, i.e. wherever eta > 0
+__device__ __forceinline__ df eta_of(df S) {
+    const df q = df_quick(1.0f, -S.hi);
+    return df{q.hi, __fsub_rn(q.lo, S.lo)};
 }
 
 // two components, double-float mu: phi of both lanes; false outside the domain
@@ -278,13 +307,13 @@ template <int FORCE>
 __device__ __forceinline__ bool mu_pair_df(float2 r, float2 lin, const DevParams &P, const float4 *s_t,
                                            DF<float2> &phi) {
     const DF<float2> b = {make_float2(P.b_hi[0], P.b_hi[1]), make_float2(P.b_lo[0], P.b_lo[1])};
-    const DF<float2> br = df_mul_f(b, r);
-    df eta = df_add(df{1.0f, 0.0f}, df_neg(df{br.hi.x, br.lo.x}));
-    eta = df_add(eta, df_neg(df{br.hi.y, br.lo.y}));
+    const DF<float2> br = df_mul_fu(b, r);
+    const df s = df_two_sum(br.hi.x, br.hi.y);
+    const df eta = eta_of(df{s.hi, __fadd_rn(s.lo, __fadd_rn(br.lo.x, br.lo.y))});
     const df rt = df_two_sum(r.x, r.y);  // the sum of two FP32 densities is exact as a pair
     const bool ok = r.x > 0.0f && r.y > 0.0f && eta.hi > 0.0f;
     const df ieta = df_recip(eta);
-    phi = mu_df_lanes<float2, FORCE>(r, lin, b, ieta, df_mul(rt, ieta), ok, P, s_t);
+    phi = mu_df_lanes<float2, FORCE>(r, lin, b, ieta, df_mul_u(rt, ieta), ok, P, s_t);
     return ok;
 }
 
@@ -292,7 +321,7 @@ template <int FORCE>
 __device__ __forceinline__ bool mu_pair_f32(float2 r, float2 lin, const DevParams &P, float2 &phi) {
     const float eta = __fmaf_rn(-P.b_hi[1], r.y, __fmaf_rn(-P.b_hi[0], r.x, 1.0f));
     const bool ok = r.x > 0.0f && r.y > 0.0f && eta > 0.0f;
-    const float ieta = 1.0f / eta;
+    const float ieta = __frcp_rn(eta);
     phi = mu_f32_lanes<float2, FORCE>(r, lin, make_float2(P.b_hi[0], P.b_hi[1]), ieta,
                                       __fmul_rn(__fadd_rn(r.x, r.y), ieta), P);
     return ok;
@@ -368,21 +397,26 @@ __device__ __forceinline__ bool mu_node(const R (&r)[N], const R (&lin)[N], cons
 #pragma unroll
         for (int c = 1; c < N; ++c) rt = __fadd_rn(rt, r[c]);
         ok = ok && eta > 0.0f;
-        const float ieta = 1.0f / eta;
+        const float ieta = __frcp_rn(eta);
         const float rte = __fmul_rn(rt, ieta);
 #pragma unroll
         for (int c = 0; c < N; ++c) phi[c] = mu_f32_lanes<float, FORCE>(r[c], lin[c], P.b_hi[c], ieta, rte, P);
     } else {  // MU_DF, one component lane at a time
-        df eta = {1.0f, 0.0f};
+        df S = df_mul_fu(df{P.b_hi[0], P.b_lo[0]}, r[0]);
 #pragma unroll
-        for (int c = 0; c < N; ++c) eta = df_add(eta, df_neg(df_mul_f(df{P.b_hi[c], P.b_lo[c]}, r[c])));
+        for (int c = 1; c < N; ++c) {
+            const df p = df_mul_fu(df{P.b_hi[c], P.b_lo[c]}, r[c]);
+            const df t = df_two_sum(S.hi, p.hi);
+            S = df{t.hi, __fadd_rn(t.lo, __fadd_rn(S.lo, p.lo))};
+        }
+        const df eta = eta_of(S);
         // total density: the sum of the first two FP32 densities is exact as a pair
         df rt = N == 1 ? df{r[0], 0.0f} : df_two_sum(r[0], r[N > 1 ? 1 : 0]);
 #pragma unroll
         for (int c = 2; c < N; ++c) rt = df_add(rt, df{r[c], 0.0f});
         ok = ok && eta.hi > 0.0f;
         const df ieta = df_recip(eta);
-        const df rte = df_mul(rt, ieta);
+        const df rte = df_mul_u(rt, ieta);
 #pragma unroll
         for (int c = 0; c < N; ++c)
             phi[c] = mu_df_lanes<float, FORCE>(r[c], lin[c], df{P.b_hi[c], P.b_lo[c]}, ieta, rte, ok, P,
@@ -422,7 +456,7 @@ __device__ __forceinline__ V dir_dot(V a, V b) {
 // One opposite pair (i, ip = -i) of the BGK collision with forcing.  With
 // A = w (drho + rho (4.5 (v.u)^2 - 1.5 u^2)), B = 3 w rho v.u, C = 4.5 w S:(vv - theta I),
 // D = 3 w v.G:  f^eq - w rho_ref = A +- B and F = C +- D (Eqs. feq, forcing terms);
-// post = (1 - omega) g + omega (f^eq - w rho_ref) + F.
+// post = (1 - omega) g + omega (f^eq - w rho_ref) + F = (1 - omega) g + (omega A + C) +- (omega B + D).
 template <int LAT, int I, class V>
 __device__ __forceinline__ void bgk_pair(V r, V drho, V u, V v, V gx, V gy, V m15, V Sxx, V Syy, V Sxy, V omega,
                                          V omc, V gi, V gip, V &pi, V &pip) {
@@ -440,8 +474,9 @@ __device__ __forceinline__ void bgk_pair(V r, V drho, V u, V v, V gx, V gy, V m1
         if constexpr (CX * CY != 0) C = v_fma(Sxy, vc<V>(9.0 * W * CX * CY), C);
     }
     const V D = v_mul(vG, vc<V>(3.0 * W));
-    pi = v_fma(omc, gi, v_fma(omega, v_add(A, B), v_add(C, D)));
-    pip = v_fma(omc, gip, v_fma(omega, v_sub(A, B), v_sub(C, D)));
+    const V even = v_fma(omega, A, C), odd = v_fma(omega, B, D);
+    pi = v_fma(omc, gi, v_add(even, odd));
+    pip = v_fma(omc, gip, v_sub(even, odd));
 }
 
 // BGK collision with forcing of one component lane.  The second forcing moment is
@@ -765,7 +800,7 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
         lap = lap_d1q3(rho, s_rho[e + 1], s_rho[e - 1]);
         grx = FORCE == 0 ? grad_d1q3(s_rho[e + 1], s_rho[e - 1]) : vc<float2>(0.0);
         gry = vc<float2>(0.0);
-        gpx = v_mul(phi_diff2(phi_at(m + 1), phi_at(m - 1)), vc<float2>(0.5));
+        gpx = v_mul(phi_diff2(phi_at(m + 1), phi_at(m - 1)), vs(P.gkt2_f, rho));
         gpy = vc<float2>(0.0);
     } else {
         const Nbr9<float2> nb = nbr9(s_rho + e, EX);
@@ -775,7 +810,7 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
         grad_d2q9_diff(phi_diff2(phi_at(m + 1), phi_at(m - 1)), phi_diff2(phi_at(m + MX), phi_at(m - MX)),
                        phi_diff2(phi_at(m + MX + 1), phi_at(m - MX - 1)),  // NE - SW
                        phi_diff2(phi_at(m - MX + 1), phi_at(m + MX - 1)),  // SE - NW
-                       gpx, gpy);
+                       vs(P.gkt3_f, rho), vs(P.gkt12_f, rho), gpx, gpy);
     }
     float2 gr[Q], post[Q];
 #pragma unroll
@@ -824,7 +859,8 @@ __device__ __forceinline__ void step_tile(const S *__restrict__ fin, S *__restri
     static_assert(MU == MU_F64 ? sizeof(R) == 8 : sizeof(R) == 4, "MU and R mismatch");
 
     __shared__ R s_rho[N][EY * EX];
-    __shared__ MT s_phi[N][MY * MX];  // gamma mu (log) or gamma mu - theta ln rho (nid)
+    // gamma mu (log) or gamma mu - theta ln rho (nid); divided by gamma kT for FP32-class mu
+    __shared__ MT s_phi[N][MY * MX];
     __shared__ __align__(16) float s_tbl[TblWords<MU>::value];
 
     const int nx = P.nx, ny = P.ny;
@@ -905,7 +941,7 @@ __device__ __forceinline__ void step_tile(const S *__restrict__ fin, S *__restri
     for (int c = 0; c < N; ++c) {
         rho[c] = s_rho[c][ey * EX + ex];
         lap[c] = lap_at<LAT, R>(s_rho[c], ex, ey, EX);
-        grad_phi<LAT, R, MT>(s_phi[c], mx, my, MX, gpx[c], gpy[c]);
+        grad_phi<LAT, R, MT>(s_phi[c], mx, my, MX, P, gpx[c], gpy[c]);
         if constexpr (FORCE == 0) grad_at<LAT, R>(s_rho[c], ex, ey, EX, grx[c], gry[c]);
         else grx[c] = gry[c] = (R)0;
     }

@@ -103,6 +103,27 @@ __device__ __forceinline__ DF<V> df_mul(DF<V> a, DF<V> b) {
     return df_quick(p.hi, lo);
 }
 
+// unnormalised products (|lo| up to about an ulp of hi), for values that only feed
+// further df arithmetic
+template <class V>
+__device__ __forceinline__ DF<V> df_mul_u(DF<V> a, DF<V> b) {
+    DF<V> p = df_two_prod(a.hi, b.hi);
+    return {p.hi, v_fma(a.hi, b.lo, v_fma(a.lo, b.hi, p.lo))};
+}
+
+template <class V>
+__device__ __forceinline__ DF<V> df_mul_fu(DF<V> a, V b) {
+    DF<V> p = df_two_prod(a.hi, b);
+    return {p.hi, v_fma(a.lo, b, p.lo)};
+}
+
+// a + b for a df a and a working-precision b
+template <class V>
+__device__ __forceinline__ DF<V> df_add_f(DF<V> a, V b) {
+    DF<V> s = df_two_sum(a.hi, b);
+    return df_quick(s.hi, v_add(s.lo, a.lo));
+}
+
 template <class V>
 __device__ __forceinline__ DF<V> df_mul_f(DF<V> a, V b) {
     DF<V> p = df_two_prod(a.hi, b);
@@ -150,12 +171,12 @@ __device__ __forceinline__ V grad_d1q3(V e, V w) {
     return v_mul(v_sub(e, w), vc<V>(0.5));
 }
 
-// D phi from the differences of phi across the node (already rounded to the lane type):
-// ew = e - w, ns = n - s, d1 = ne - sw, d2 = se - nw.
+// s D phi from the differences of phi across the node (already rounded to the lane type):
+// ew = e - w, ns = n - s, d1 = ne - sw, d2 = se - nw; c3 = s/3, c12 = s/12.
 template <class V>
-__device__ __forceinline__ void grad_d2q9_diff(V ew, V ns, V d1, V d2, V &gx, V &gy) {
-    gx = v_fma(ew, vc<V>(1.0 / 3.0), v_mul(v_add(d1, d2), vc<V>(1.0 / 12.0)));
-    gy = v_fma(ns, vc<V>(1.0 / 3.0), v_mul(v_sub(d1, d2), vc<V>(1.0 / 12.0)));
+__device__ __forceinline__ void grad_d2q9_diff(V ew, V ns, V d1, V d2, V c3, V c12, V &gx, V &gy) {
+    gx = v_fma(ew, c3, v_mul(v_add(d1, d2), c12));
+    gy = v_fma(ns, c3, v_mul(v_sub(d1, d2), c12));
 }
 
 }  // namespace lbvdw

@@ -85,15 +85,15 @@ __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (do
 
 __device__ __forceinline__ float df_to_float(df a) { return __fadd_rn(a.hi, a.lo); }
 
-// 1/a: float reciprocal refined by one Newton step in df arithmetic
+// 1/a for a positive df a (possibly unnormalised).  y ~ 1/a.hi from the MUFU approximation
+// and one Newton step lies within an ulp of 1/a.hi, so the residual 1 - a.hi y is exact in
+// one fused multiply-add; with e = 1 - a y, 1/a = y (1 + e + e^2 + ...), and the e^3 term
+// lies below the df precision.  The result is unnormalised: hi = y, |lo| ~ ulp(y).
 __device__ __forceinline__ df df_recip(df a) {
-    float y = __frcp_rn(a.hi);
-    // e = 1 - a*y in df, then y + y*e
-    df ay = df_mul_f(a, y);
-    df e = df_add(df{1.0f, 0.0f}, df_neg(ay));
-    df ye = df_two_prod(y, e.hi);
-    ye.lo = __fmaf_rn(y, e.lo, ye.lo);
-    return df_add(df{y, 0.0f}, df_quick(ye.hi, ye.lo));
+    const float y0 = __fdividef(1.0f, a.hi);
+    const float y = __fmaf_rn(y0, __fmaf_rn(-a.hi, y0, 1.0f), y0);
+    const float e = __fmaf_rn(-a.lo, y, __fmaf_rn(-a.hi, y, 1.0f));
+    return df{y, __fmul_rn(y, __fmaf_rn(e, e, e))};
 }
 
 // The per-lane part of the table reduction: x_hi = 2^e m, j = top 7 bits of the mantissa;

@@ -104,11 +104,14 @@ __device__ __forceinline__ void grad_rows(const T *s, const T *m, const T *n, in
 }
 
 template <class R, class T>
-__device__ __forceinline__ void grad_phi_rows(const T *s, const T *m, const T *n, int x, R &gx, R &gy) {
+__device__ __forceinline__ void grad_phi_rows(const T *s, const T *m, const T *n, int x, const DevParams &P, R &gx,
+                                              R &gy) {
+    R c3, c12, c2;
+    phi_weights<R, T>(P, c3, c12, c2);
     grad_d2q9_diff(phi_diff<R>(m[x + 1], m[x - 1]), phi_diff<R>(n[x], s[x]),
                    phi_diff<R>(n[x + 1], s[x - 1]),  // NE - SW
                    phi_diff<R>(s[x + 1], n[x - 1]),  // SE - NW
-                   gx, gy);
+                   c3, c12, gx, gy);
 }
 
 // ---------------------------------------------------------------------------
@@ -303,7 +306,7 @@ __global__ void __launch_bounds__(StripLayout<N, TX, TY, MU>::NT, 2)
                 if constexpr (FORCE == 0) grad_rows<R>(rb + rs * RW, rb + rm * RW, rb + rn * RW, ex, grx[c], gry[c]);
                 else grx[c] = gry[c] = (R)0;
                 const MT *pb = s_phi + (size_t)c * RING * MW;
-                grad_phi_rows<R, MT>(pb + rs * MW, pb + rm * MW, pb + rn * MW, col + 1, gpx[c], gpy[c]);
+                grad_phi_rows<R, MT>(pb + rs * MW, pb + rm * MW, pb + rn * MW, col + 1, P, gpx[c], gpy[c]);
             }
             collide_node<2, N, R, FORCE>(rho, lap, gpx, gpy, grx, gry, jx, jy, P, gr, post);
             const int xe = x + 1 == nx ? 0 : x + 1, xw = x == 0 ? nx - 1 : x - 1;
