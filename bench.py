@@ -70,9 +70,12 @@ def parse(argv=None):
 # step kernel, from an ncu capture of this script (the profile file named beside it).  The
 # value holds for the kernel sources whose digest is recorded with it and is reported as
 # null once they change.
-KERNEL_SOURCES = ("lb_kernels.cuh", "lb_mu.cuh", "lb_tu.cuh", "lb_launch.cuh", "lb_d2q9_df.cu")
-TRAFFIC = {"fp32_dfmu": {"digest": "e2dc21e0f2b6a23c6cbb8e2c9d2f9659c375c5ac442c0d2972d5f05824a8105e",
-                         "bytes": 108601856, "warp_instructions": 48537600, "issue_active": 0.713,
+KERNEL_SOURCES = ("lb_kernels.cuh", "lb_lane.cuh", "lb_mu.cuh", "lb_tu.cuh", "lb_launch.cuh", "lb_d2q9_df.cu")
+TRAFFIC = {"fp32_dfmu": {"digest": "0ee2b91ec163041d2b6bfd1bda5b445859ae3b5a9d738645f0a2dd3a141661bf",
+                         "bytes": 107706368, "warp_instructions": 29409280, "issue_active": 0.568,
+                         "fma_pipe_active": 0.502,
+                         "stalls_per_issue": {"barrier": 3.18, "not_selected": 2.53, "long_scoreboard": 2.48,
+                                              "math_pipe_throttle": 2.09, "mio_throttle": 1.21},
                          "profile": "profiles/lb_step_kernel_fp32_dfmu_c2_1024.md"}}
 # instruction issue peak of the GPU: 152 SMs x 4 schedulers x 2.07 GHz (one warp instruction
 # per scheduler per cycle)
@@ -97,14 +100,17 @@ def traffic_of(precision):
 
 
 def limiter_of(precision, alg_bytes, peak_gbs):
-    """What bounds the step kernel, from the same ncu capture: its warp instructions per
-    launch at the GPU's peak issue rate, and the HBM fraction that would allow."""
+    """What bounds the step kernel, from the same ncu capture: how busy instruction issue
+    and the FMA pipe are, the largest warp stall reasons, and the HBM fraction the launch's
+    warp instructions would allow at the GPU's peak issue rate."""
     rec = TRAFFIC.get(precision)
     if not rec or rec["digest"] != kernel_digest():
         return None
     t_issue = rec["warp_instructions"] / ISSUE_PEAK
-    return {"kind": "instruction issue", "warp_instructions_per_launch": rec["warp_instructions"],
-            "issue_active": rec["issue_active"], "launch_time_at_peak_issue_us": t_issue * 1e6,
+    return {"kind": "latency (barriers between the phases, global-load waits, FMA-pipe bursts)",
+            "warp_instructions_per_launch": rec["warp_instructions"], "issue_active": rec["issue_active"],
+            "fma_pipe_active": rec["fma_pipe_active"], "stalls_per_issue": rec["stalls_per_issue"],
+            "launch_time_at_peak_issue_us": t_issue * 1e6,
             "hbm_frac_at_peak_issue": alg_bytes / t_issue / 1e9 / peak_gbs, "profile": rec["profile"]}
 
 

@@ -973,11 +973,12 @@ __device__ __forceinline__ void step_tile(const S *__restrict__ fin, S *__restri
     }
 }
 
-// FP32 storage with up to two components: ask for five resident 256-thread CTAs per SM
-// (48 registers); more resident warps hide the barrier waits between the phases.
+// FP32 storage, 256-thread tiles: ask for five resident CTAs per SM with up to two
+// components (48 registers), two with three or four (128 registers); more resident warps
+// hide the barrier waits between the phases.
 template <class S, int N, int NT>
 struct MinBlocks {
-    static constexpr int value = (sizeof(S) == 4 && N <= 2 && NT == 256) ? 5 : 1;
+    static constexpr int value = (sizeof(S) == 4 && NT == 256) ? (N <= 2 ? 5 : 2) : 1;
 };
 
 template <int LAT, int N, int TX, int TY, class S, class R, int FORCE, int MU>
