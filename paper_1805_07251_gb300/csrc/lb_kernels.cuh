@@ -253,12 +253,28 @@ __device__ __forceinline__ void lin_node(const R (&r)[N], const R (&lp)[N], cons
         lin[c] = t;
     }
 }
-// the same for a two-component pair, both components in one lane pair
-__device__ __forceinline__ float2 lin_pair(float2 r, float2 lp, const DevParams &P) {
-    float2 t = v_mul(make_float2(P.kappa_f[0], P.kappa_f[4]), vs(lp.x, r));
-    t = v_fma(make_float2(P.a2_f[0], P.a2_f[4]), vs(r.x, r), t);
-    t = v_fma(make_float2(P.kappa_f[1], P.kappa_f[5]), vs(lp.y, r), t);
-    return v_fma(make_float2(P.a2_f[1], P.a2_f[5]), vs(r.y, r), t);
+// component c of NP lane pairs (pair c / 2, half c % 2)
+template <int NP>
+__device__ __forceinline__ float comp(const float2 (&v)[NP], int c) {
+    return (c & 1) ? v[c >> 1].y : v[c >> 1].x;
+}
+
+// the same for NP component pairs, components 2q and 2q+1 in lane pair q
+template <int NP>
+__device__ __forceinline__ void lin_pairs(const float2 (&r)[NP], const float2 (&lp)[NP], const DevParams &P,
+                                          float2 (&lin)[NP]) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const int c0 = 8 * q, c1 = 8 * q + 4;  // rows 2q and 2q+1 of the stride-4 matrices
+        float2 t = v_mul(make_float2(P.kappa_f[c0], P.kappa_f[c1]), vs(lp[0].x, r[0]));
+        t = v_fma(make_float2(P.a2_f[c0], P.a2_f[c1]), vs(r[0].x, r[0]), t);
+#pragma unroll
+        for (int cc = 1; cc < 2 * NP; ++cc) {
+            t = v_fma(make_float2(P.kappa_f[c0 + cc], P.kappa_f[c1 + cc]), vs(comp(lp, cc), r[0]), t);
+            t = v_fma(make_float2(P.a2_f[c0 + cc], P.a2_f[c1 + cc]), vs(comp(r, cc), r[0]), t);
+        }
+        lin[q] = t;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -302,28 +318,59 @@ __device__ __forceinline__ df eta_of(df S) {
     return df{q.hi, __fsub_rn(q.lo, S.lo)};
 }
 
-// two components, double-float mu: phi of both lanes; false outside the domain
-template <int FORCE>
-__device__ __forceinline__ bool mu_pair_df(float2 r, float2 lin, const DevParams &P, const float4 *s_t,
-                                           DF<float2> &phi) {
-    const DF<float2> b = {make_float2(P.b_hi[0], P.b_hi[1]), make_float2(P.b_lo[0], P.b_lo[1])};
-    const DF<float2> br = df_mul_fu(b, r);
-    const df s = df_two_sum(br.hi.x, br.hi.y);
-    const df eta = eta_of(df{s.hi, __fadd_rn(s.lo, __fadd_rn(br.lo.x, br.lo.y))});
-    const df rt = df_two_sum(r.x, r.y);  // the sum of two FP32 densities is exact as a pair
-    const bool ok = r.x > 0.0f && r.y > 0.0f && eta.hi > 0.0f;
+// NP component pairs, double-float mu: phi of every lane; false outside the domain.
+// S = sum_c b^c rho^c and rho = sum_c rho^c accumulate in component order.
+template <int NP, int FORCE>
+__device__ __forceinline__ bool mu_pairs_df(const float2 (&r)[NP], const float2 (&lin)[NP], const DevParams &P,
+                                            const float4 *s_t, DF<float2> (&phi)[NP]) {
+    DF<float2> b[NP], br[NP];
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        b[q] = {make_float2(P.b_hi[2 * q], P.b_hi[2 * q + 1]), make_float2(P.b_lo[2 * q], P.b_lo[2 * q + 1])};
+        br[q] = df_mul_fu(b[q], r[q]);
+        ok = ok && r[q].x > 0.0f && r[q].y > 0.0f;
+    }
+    df S = {br[0].hi.x, br[0].lo.x};
+#pragma unroll
+    for (int c = 1; c < 2 * NP; ++c) {
+        const float ph = (c & 1) ? br[c >> 1].hi.y : br[c >> 1].hi.x;
+        const float pl = (c & 1) ? br[c >> 1].lo.y : br[c >> 1].lo.x;
+        const df t = df_two_sum(S.hi, ph);
+        S = df{t.hi, __fadd_rn(t.lo, __fadd_rn(S.lo, pl))};
+    }
+    const df eta = eta_of(S);
+    // total density: the sum of the first two FP32 densities is exact as a pair
+    df rt = df_two_sum(r[0].x, r[0].y);
+#pragma unroll
+    for (int c = 2; c < 2 * NP; ++c) rt = df_add(rt, df{comp(r, c), 0.0f});
+    ok = ok && eta.hi > 0.0f;
     const df ieta = df_recip(eta);
-    phi = mu_df_lanes<float2, FORCE>(r, lin, b, ieta, df_mul_u(rt, ieta), ok, P, s_t);
+    const df rte = df_mul_u(rt, ieta);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) phi[q] = mu_df_lanes<float2, FORCE>(r[q], lin[q], b[q], ieta, rte, ok, P, s_t);
     return ok;
 }
 
-template <int FORCE>
-__device__ __forceinline__ bool mu_pair_f32(float2 r, float2 lin, const DevParams &P, float2 &phi) {
-    const float eta = __fmaf_rn(-P.b_hi[1], r.y, __fmaf_rn(-P.b_hi[0], r.x, 1.0f));
-    const bool ok = r.x > 0.0f && r.y > 0.0f && eta > 0.0f;
+template <int NP, int FORCE>
+__device__ __forceinline__ bool mu_pairs_f32(const float2 (&r)[NP], const float2 (&lin)[NP], const DevParams &P,
+                                             float2 (&phi)[NP]) {
+    float eta = 1.0f, rt = r[0].x;
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 2 * NP; ++c) {
+        eta = __fmaf_rn(-P.b_hi[c], comp(r, c), eta);
+        ok = ok && comp(r, c) > 0.0f;
+    }
+#pragma unroll
+    for (int c = 1; c < 2 * NP; ++c) rt = __fadd_rn(rt, comp(r, c));
+    ok = ok && eta > 0.0f;
     const float ieta = __frcp_rn(eta);
-    phi = mu_f32_lanes<float2, FORCE>(r, lin, make_float2(P.b_hi[0], P.b_hi[1]), ieta,
-                                      __fmul_rn(__fadd_rn(r.x, r.y), ieta), P);
+    const float rte = __fmul_rn(rt, ieta);
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+        phi[q] = mu_f32_lanes<float2, FORCE>(r[q], lin[q], make_float2(P.b_hi[2 * q], P.b_hi[2 * q + 1]), ieta,
+                                             rte, P);
     return ok;
 }
 
@@ -377,18 +424,30 @@ __device__ __forceinline__ bool mu_node(const R (&r)[N], const R (&lin)[N], cons
                                         : 0.0);
             phi[c] = ph;
         }
-    } else if constexpr (N == 2) {  // MU_DF / MU_F32: both components in one lane pair
-        const float2 r2 = make_float2(r[0], r[1]), l2 = make_float2(lin[0], lin[1]);
+    } else if constexpr (N % 2 == 0) {  // MU_DF / MU_F32: components in lane pairs
+        constexpr int NP = N / 2;
+        float2 r2[NP], l2[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            r2[q] = make_float2(r[2 * q], r[2 * q + 1]);
+            l2[q] = make_float2(lin[2 * q], lin[2 * q + 1]);
+        }
         if constexpr (MU == MU_DF) {
-            DF<float2> ph;
-            ok = mu_pair_df<FORCE>(r2, l2, P, reinterpret_cast<const float4 *>(s_tbl), ph);
-            phi[0] = df{ph.hi.x, ph.lo.x};
-            phi[1] = df{ph.hi.y, ph.lo.y};
+            DF<float2> ph[NP];
+            ok = mu_pairs_df<NP, FORCE>(r2, l2, P, reinterpret_cast<const float4 *>(s_tbl), ph);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                phi[2 * q] = df{ph[q].hi.x, ph[q].lo.x};
+                phi[2 * q + 1] = df{ph[q].hi.y, ph[q].lo.y};
+            }
         } else {
-            float2 ph;
-            ok = mu_pair_f32<FORCE>(r2, l2, P, ph);
-            phi[0] = ph.x;
-            phi[1] = ph.y;
+            float2 ph[NP];
+            ok = mu_pairs_f32<NP, FORCE>(r2, l2, P, ph);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                phi[2 * q] = ph[q].x;
+                phi[2 * q + 1] = ph[q].y;
+            }
         }
     } else if constexpr (MU == MU_F32) {
         float eta = 1.0f, rt = r[0];
@@ -549,26 +608,114 @@ __device__ __forceinline__ void friction_two(T k, T (&G)[2], const T (&u)[2], co
     G[1] = v_add(G[1], v_mul(k, d));
 }
 
-// One node of phase 3 for two components in one lane pair: from rho, Lap rho, D phi,
-// D rho ("log" force) and the bare momenta, the total gain G (mean field + implicit
-// friction), then Psi, the forcing populations and the BGK collision.  g holds the
-// node's stored populations (deviations); post receives the post-collision deviations.
-template <int LAT, int FORCE>
-__device__ __forceinline__ void collide_pair(float2 rho, float2 lap, float2 gpx, float2 gpy, float2 grx, float2 gry,
-                                             float2 jx, float2 jy, const DevParams &P,
-                                             const float2 (&g)[Lat<LAT>::Q], float2 (&post)[Lat<LAT>::Q]) {
-    float2 Gx, Gy, ir, ux, uy;
-    gain_lane<FORCE>(rho, gpx, gpy, grx, gry, jx, jy, Gx, Gy, ir, ux, uy);
-    const float k = friction_k(rho.x, rho.y, P.lam_fr_f);
-    Gx = friction_pair(k, Gx, ux, ir);
-    if constexpr (LAT == 2) Gy = friction_pair(k, Gy, uy, ir);
-    bgk_lane<LAT, float2>(rho, ux, uy, Gx, Gy, lap, ir, make_float2(P.rho_ref_f[0], P.rho_ref_f[1]),
-                          make_float2(P.omega_f, P.omega_f), make_float2(P.omc_f, P.omc_f),
-                          make_float2(P.psi_g_f, P.psi_g_f), make_float2(P.psi_l_f, P.psi_l_f), g, post);
+// Friction of N > 2 components, one component per lane: (D + L/2) h = -L u0, G^f = D h per
+// direction (Eq. forceFriction), with W^{cc'} = lambda^{cc'} rho^c rho^c' / (rho^c + rho^c'),
+// L the weighted Laplacian of W and u0 = u + G / (2 rho).  D + L/2 is symmetric positive
+// definite: elimination without pivoting.
+template <int N, int DIM, class T>
+__device__ __forceinline__ void friction_n(const T (&rho)[N], const T (&ir)[N], const T (&ux)[N], const T (&uy)[N],
+                                           const DevParams &P, T (&Gx)[N], T (&Gy)[N]) {
+    T W[N][N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        W[c][c] = vc<T>(0.0);
+#pragma unroll
+        for (int cc = c + 1; cc < N; ++cc) {
+            const T lam = pv<T>(P.lam[c * 4 + cc], P.lam_f[c * 4 + cc]);
+            W[c][cc] = v_mul(v_mul(v_mul(lam, rho[c]), rho[cc]), v_rcp(v_add(rho[c], rho[cc])));
+            W[cc][c] = W[c][cc];
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        T u0[N], M[N][N], h[N];
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            const T gg = d == 0 ? Gx[c] : Gy[c];
+            u0[c] = v_fma(v_mul(gg, vc<T>(0.5)), ir[c], d == 0 ? ux[c] : uy[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            T diag = rho[c], rhs = vc<T>(0.0);
+#pragma unroll
+            for (int cc = 0; cc < N; ++cc) {
+                if (cc == c) continue;
+                M[c][cc] = v_mul(W[c][cc], vc<T>(-0.5));
+                diag = v_fma(W[c][cc], vc<T>(0.5), diag);
+                rhs = v_fma(v_neg(W[c][cc]), v_sub(u0[c], u0[cc]), rhs);
+            }
+            M[c][c] = diag;
+            h[c] = rhs;
+        }
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const T inv = v_rcp(M[k][k]);
+#pragma unroll
+            for (int r2 = k + 1; r2 < N; ++r2) {
+                const T m = v_mul(M[r2][k], inv);
+#pragma unroll
+                for (int c2 = k + 1; c2 < N; ++c2) M[r2][c2] = v_fma(v_neg(m), M[k][c2], M[r2][c2]);
+                h[r2] = v_fma(v_neg(m), h[k], h[r2]);
+            }
+        }
+#pragma unroll
+        for (int k = N - 1; k >= 0; --k) {
+            T sacc = h[k];
+#pragma unroll
+            for (int c2 = k + 1; c2 < N; ++c2) sacc = v_fma(v_neg(M[k][c2]), h[c2], sacc);
+            h[k] = v_mul(sacc, v_rcp(M[k][k]));
+        }
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            if (d == 0) Gx[c] = v_fma(rho[c], h[c], Gx[c]);
+            else Gy[c] = v_fma(rho[c], h[c], Gy[c]);
+        }
+    }
 }
 
-// One node of phase 3, N components (arrays over c); two FP32 components go through the
-// lane-pair form above, with bitwise the same result as one component at a time.
+// One node of phase 3 for NP component pairs (components 2q, 2q+1 in lane pair q): from rho,
+// Lap rho, D phi, D rho ("log" force) and the bare momenta, the total gain G (mean field +
+// implicit friction), then Psi, the forcing populations and the BGK collision.  g holds
+// the node's stored populations (deviations); post receives the post-collision deviations.
+template <int LAT, int NP, int FORCE>
+__device__ __forceinline__ void collide_pairs(const float2 (&rho)[NP], const float2 (&lap)[NP],
+                                              const float2 (&gpx)[NP], const float2 (&gpy)[NP],
+                                              const float2 (&grx)[NP], const float2 (&gry)[NP],
+                                              const float2 (&jx)[NP], const float2 (&jy)[NP], const DevParams &P,
+                                              const float2 (&g)[NP][Lat<LAT>::Q], float2 (&post)[NP][Lat<LAT>::Q]) {
+    float2 Gx[NP], Gy[NP], ir[NP], ux[NP], uy[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+        gain_lane<FORCE>(rho[q], gpx[q], gpy[q], grx[q], gry[q], jx[q], jy[q], Gx[q], Gy[q], ir[q], ux[q], uy[q]);
+    if constexpr (NP == 1) {
+        const float k = friction_k(rho[0].x, rho[0].y, P.lam_fr_f);
+        Gx[0] = friction_pair(k, Gx[0], ux[0], ir[0]);
+        if constexpr (LAT == 2) Gy[0] = friction_pair(k, Gy[0], uy[0], ir[0]);
+    } else {
+        constexpr int N = 2 * NP;
+        float r1[N], i1[N], ux1[N], uy1[N], gx1[N], gy1[N];
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            r1[c] = comp(rho, c), i1[c] = comp(ir, c), ux1[c] = comp(ux, c), uy1[c] = comp(uy, c);
+            gx1[c] = comp(Gx, c), gy1[c] = comp(Gy, c);
+        }
+        friction_n<N, Lat<LAT>::D, float>(r1, i1, ux1, uy1, P, gx1, gy1);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            Gx[q] = make_float2(gx1[2 * q], gx1[2 * q + 1]);
+            Gy[q] = make_float2(gy1[2 * q], gy1[2 * q + 1]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+        bgk_lane<LAT, float2>(rho[q], ux[q], uy[q], Gx[q], Gy[q], lap[q], ir[q],
+                              make_float2(P.rho_ref_f[2 * q], P.rho_ref_f[2 * q + 1]),
+                              make_float2(P.omega_f, P.omega_f), make_float2(P.omc_f, P.omc_f),
+                              make_float2(P.psi_g_f, P.psi_g_f), make_float2(P.psi_l_f, P.psi_l_f), g[q], post[q]);
+}
+
+// One node of phase 3, N components (arrays over c); an even number of FP32 components goes
+// through the lane-pair form above, with bitwise the same result as one component at a time.
 template <int LAT, int N, class R, int FORCE>
 __device__ __forceinline__ void collide_node(const R (&rho)[N], const R (&lap)[N], const R (&gpx)[N],
                                              const R (&gpy)[N], const R (&grx)[N], const R (&gry)[N],
@@ -576,20 +723,27 @@ __device__ __forceinline__ void collide_node(const R (&rho)[N], const R (&lap)[N
                                              const R (&g)[N][Lat<LAT>::Q], R (&post)[N][Lat<LAT>::Q]) {
     using L = Lat<LAT>;
     constexpr int Q = L::Q;
-    if constexpr (N == 2 && sizeof(R) == 4) {
-        float2 g2[Q], p2[Q];
+    if constexpr (N % 2 == 0 && sizeof(R) == 4) {
+        constexpr int NP = N / 2;
+        float2 r2[NP], l2[NP], px[NP], py[NP], qx[NP], qy[NP], ax[NP], ay[NP], g2[NP][Q], p2[NP][Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) g2[i] = make_float2(g[0][i], g[1][i]);
-        collide_pair<LAT, FORCE>(make_float2(rho[0], rho[1]), make_float2(lap[0], lap[1]),
-                                 make_float2(gpx[0], gpx[1]), make_float2(gpy[0], gpy[1]),
-                                 make_float2(grx[0], grx[1]), make_float2(gry[0], gry[1]),
-                                 make_float2(jx[0], jx[1]), make_float2(jy[0], jy[1]), P, g2, p2);
+        for (int q = 0; q < NP; ++q) {
+            const int c = 2 * q;
+            r2[q] = make_float2(rho[c], rho[c + 1]), l2[q] = make_float2(lap[c], lap[c + 1]);
+            px[q] = make_float2(gpx[c], gpx[c + 1]), py[q] = make_float2(gpy[c], gpy[c + 1]);
+            qx[q] = make_float2(grx[c], grx[c + 1]), qy[q] = make_float2(gry[c], gry[c + 1]);
+            ax[q] = make_float2(jx[c], jx[c + 1]), ay[q] = make_float2(jy[c], jy[c + 1]);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            post[0][i] = p2[i].x;
-            post[1][i] = p2[i].y;
+            for (int i = 0; i < Q; ++i) g2[q][i] = make_float2(g[c][i], g[c + 1][i]);
         }
-        return;
+        collide_pairs<LAT, NP, FORCE>(r2, l2, px, py, qx, qy, ax, ay, P, g2, p2);
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                post[2 * q][i] = p2[q][i].x;
+                post[2 * q + 1][i] = p2[q][i].y;
+            }
     } else {
         R ux[N], uy[N], Gx[N], Gy[N], ir[N];
 #pragma unroll
@@ -600,60 +754,7 @@ __device__ __forceinline__ void collide_node(const R (&rho)[N], const R (&lap)[N
             friction_two(k, Gx, ux, ir);
             if constexpr (L::D == 2) friction_two(k, Gy, uy, ir);
         } else if constexpr (N > 2) {
-            R W[N][N];
-#pragma unroll
-            for (int c = 0; c < N; ++c)
-#pragma unroll
-                for (int cc = 0; cc < N; ++cc)
-                    W[c][cc] = (c == cc) ? (R)0
-                                         : pv<R>(P.lam[c * 4 + cc], P.lam_f[c * 4 + cc]) * rho[c] * rho[cc] *
-                                               rcp(rho[c] + rho[cc]);
-#pragma unroll
-            for (int d = 0; d < L::D; ++d) {
-                R u0[N], M[N][N], h[N];
-#pragma unroll
-                for (int c = 0; c < N; ++c) {
-                    R uu = d == 0 ? ux[c] : uy[c];
-                    R gg = d == 0 ? Gx[c] : Gy[c];
-                    u0[c] = uu + (R)0.5 * gg * rcp(rho[c]);
-                }
-#pragma unroll
-                for (int c = 0; c < N; ++c) {
-                    R diag = rho[c], rhs = (R)0;
-#pragma unroll
-                    for (int cc = 0; cc < N; ++cc) {
-                        M[c][cc] = (R)(-0.5) * W[c][cc];
-                        diag += (R)0.5 * W[c][cc];
-                        rhs -= W[c][cc] * (u0[c] - u0[cc]);
-                    }
-                    M[c][c] = diag;
-                    h[c] = rhs;
-                }
-                // symmetric positive definite: elimination without pivoting
-#pragma unroll
-                for (int k = 0; k < N; ++k) {
-                    R inv = rcp(M[k][k]);
-#pragma unroll
-                    for (int r2 = k + 1; r2 < N; ++r2) {
-                        R m = M[r2][k] * inv;
-#pragma unroll
-                        for (int c2 = k + 1; c2 < N; ++c2) M[r2][c2] -= m * M[k][c2];
-                        h[r2] -= m * h[k];
-                    }
-                }
-#pragma unroll
-                for (int k = N - 1; k >= 0; --k) {
-                    R sacc = h[k];
-#pragma unroll
-                    for (int c2 = k + 1; c2 < N; ++c2) sacc -= M[k][c2] * h[c2];
-                    h[k] = sacc * rcp(M[k][k]);
-                }
-#pragma unroll
-                for (int c = 0; c < N; ++c) {
-                    if (d == 0) Gx[c] += rho[c] * h[c];
-                    else Gy[c] += rho[c] * h[c];
-                }
-            }
+            friction_n<N, L::D, R>(rho, ir, ux, uy, P, Gx, Gy);
         }
         const R omega = pv<R>(P.omega, P.omega_f), omc = pv<R>(P.omc, P.omc_f);
         const R cg = pv<R>(P.psi_g, P.psi_g_f), cl = pv<R>(P.psi_l, P.psi_l_f);
@@ -695,12 +796,12 @@ struct TileGeom {
     }
 };
 
-// The fused step, two FP32 components in lane pairs: every per-node quantity of the two
-// components lives in one register pair (densities, momenta, mu, forces, populations) and
-// is computed by the packed FP32x2 instructions; shared memory holds the pairs
-// interleaved, so one 8-byte (16-byte for double-float mu) access moves both components.
-// Same arithmetic as the general step_tile below, bitwise.
-template <int LAT, int TX, int TY, int FORCE, int MU>
+// The fused step, FP32 components in lane pairs (NP pairs: components 2q and 2q+1 in pair q):
+// every per-node quantity of a pair lives in one register pair (densities, momenta, mu,
+// forces, populations) and is computed by the packed FP32x2 instructions; shared memory
+// holds the pairs interleaved, so one 8-byte (16-byte for double-float mu) access moves
+// both components.  Same arithmetic as the general step_tile below, bitwise.
+template <int LAT, int NP, int TX, int TY, int FORCE, int MU>
 __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, float *__restrict__ fout,
                                                const DevParams &P, int x0, int y0) {
     using L = Lat<LAT>;
@@ -709,13 +810,13 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
     static_assert(MU == MU_DF || MU == MU_F32, "lane pairs need an FP32-class mu");
     using PT = typename std::conditional<MU == MU_DF, float4, float2>::type;  // phi pair: (hi, hi, lo, lo) / (x, y)
 
-    // the node's own populations wait in shared memory between phases 1 and 3 (tiles of up
-    // to 256 threads), else in registers
-    constexpr bool STAGE = NT <= 256;
+    // the node's own populations wait in shared memory between phases 1 and 3 (one pair,
+    // tiles of up to 256 threads), else in registers
+    constexpr bool STAGE = NP == 1 && NT <= 256;
     __shared__ float2 s_g[STAGE ? Q : 1][STAGE ? NT : 1];
-    float2 gk[STAGE ? 1 : Q];
-    __shared__ float2 s_rho[G::EY * EX];
-    __shared__ PT s_phi[MY * MX];
+    float2 gk[STAGE ? 1 : NP][STAGE ? 1 : Q];
+    __shared__ float2 s_rho[NP][G::EY * EX];
+    __shared__ PT s_phi[NP][MY * MX];
     __shared__ __align__(16) float s_tbl[TblWords<MU>::value];
 
     const int nx = P.nx, ny = P.ny;
@@ -727,23 +828,29 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
     const size_t plane = (size_t)nx * (size_t)ny;
     const size_t cq = (size_t)Q * plane;  // component stride
     const bool small = nx <= TX + 1 || (LAT == 2 && ny <= TY + 1);
-    const float2 rref = make_float2(P.rho_ref_f[0], P.rho_ref_f[1]);
+    float2 rref[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) rref[q] = make_float2(P.rho_ref_f[2 * q], P.rho_ref_f[2 * q + 1]);
 
     // ---- phase 1a: own node -> shared (populations, densities) ------------------
-    float2 jx, jy;
+    float2 jx[NP], jy[NP];
     {
         const int gx = small ? wrap(x, nx) : wrap1(x, nx);
         const int gy = LAT == 1 ? 0 : (small ? wrap(y, ny) : wrap1(y, ny));
         const float *src = fin + (size_t)gy * nx + gx;
-        float2 gv[Q], acc;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            gv[i] = make_float2(src[(size_t)i * plane], src[cq + (size_t)i * plane]);
-            if constexpr (STAGE) s_g[i][tid] = gv[i];
-            else gk[i] = gv[i];
+        for (int q = 0; q < NP; ++q) {
+            const float *sq = src + 2 * q * cq;
+            float2 gv[Q], acc;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                gv[i] = make_float2(sq[(size_t)i * plane], sq[cq + (size_t)i * plane]);
+                if constexpr (STAGE) s_g[i][tid] = gv[i];
+                else gk[q][i] = gv[i];
+            }
+            moments_lane<LAT>(gv, acc, jx[q], jy[q]);
+            s_rho[q][(ty + 2 * HY) * EX + tx + 2] = v_add(rref[q], acc);
         }
-        moments_lane<LAT>(gv, acc, jx, jy);
-        s_rho[(ty + 2 * HY) * EX + tx + 2] = v_add(rref, acc);
     }
     // ---- phase 1b: densities on the 2-node ring ---------------------------------
     for (int k = tid; k < G::RING; k += NT) {
@@ -752,10 +859,14 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
         const int gx = small ? wrap(x0 + ex - 2, nx) : wrap1(x0 + ex - 2, nx);
         const int gy = (LAT == 1) ? 0 : (small ? wrap(y0 + ey - 2, ny) : wrap1(y0 + ey - 2, ny));
         const float *src = fin + (size_t)gy * nx + gx;
-        float2 acc = make_float2(src[0], src[cq]);
 #pragma unroll
-        for (int i = 1; i < Q; ++i) acc = v_add(acc, make_float2(src[(size_t)i * plane], src[cq + (size_t)i * plane]));
-        s_rho[ey * EX + ex] = v_add(rref, acc);
+        for (int q = 0; q < NP; ++q) {
+            const float *sq = src + 2 * q * cq;
+            float2 acc = make_float2(sq[0], sq[cq]);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) acc = v_add(acc, make_float2(sq[(size_t)i * plane], sq[cq + (size_t)i * plane]));
+            s_rho[q][ey * EX + ex] = v_add(rref[q], acc);
+        }
     }
     __syncthreads();
 
@@ -764,19 +875,24 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
     for (int k = tid; k < MX * MY; k += NT) {
         const int mx = k % MX, my = k / MX;
         const int e = (my + HY) * EX + mx + 1;
-        const float2 r = s_rho[e];
-        float2 lp;
-        if constexpr (LAT == 1) lp = lap_d1q3(r, s_rho[e + 1], s_rho[e - 1]);
-        else lp = lap_d2q9(nbr9(s_rho + e, EX));
-        const float2 lin = lin_pair(r, lp, P);
+        float2 r[NP], lp[NP], lin[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            r[q] = s_rho[q][e];
+            if constexpr (LAT == 1) lp[q] = lap_d1q3(r[q], s_rho[q][e + 1], s_rho[q][e - 1]);
+            else lp[q] = lap_d2q9(nbr9(s_rho[q] + e, EX));
+        }
+        lin_pairs<NP>(r, lp, P, lin);
         if constexpr (MU == MU_DF) {
-            DF<float2> ph;
-            if (!mu_pair_df<FORCE>(r, lin, P, reinterpret_cast<const float4 *>(s_tbl), ph)) bad = 1;
-            s_phi[k] = make_float4(ph.hi.x, ph.hi.y, ph.lo.x, ph.lo.y);
+            DF<float2> ph[NP];
+            if (!mu_pairs_df<NP, FORCE>(r, lin, P, reinterpret_cast<const float4 *>(s_tbl), ph)) bad = 1;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) s_phi[q][k] = make_float4(ph[q].hi.x, ph[q].hi.y, ph[q].lo.x, ph[q].lo.y);
         } else {
-            float2 ph;
-            if (!mu_pair_f32<FORCE>(r, lin, P, ph)) bad = 1;
-            s_phi[k] = ph;
+            float2 ph[NP];
+            if (!mu_pairs_f32<NP, FORCE>(r, lin, P, ph)) bad = 1;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) s_phi[q][k] = ph[q];
         }
     }
     __syncthreads();
@@ -786,39 +902,46 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
     // ---- phase 3: forces, collision, streaming ----------------------------------
     const int e = (ty + 2 * HY) * EX + tx + 2;
     const int m = (ty + HY) * MX + tx + 1;
-    const float2 rho = s_rho[e];
-    float2 lap, grx, gry, gpx, gpy;
-    auto phi_at = [&](int k) {
-        if constexpr (MU == MU_DF) {
-            const float4 t = s_phi[k];
-            return DF<float2>{make_float2(t.x, t.y), make_float2(t.z, t.w)};
-        } else {
-            return s_phi[k];
-        }
-    };
-    if constexpr (LAT == 1) {
-        lap = lap_d1q3(rho, s_rho[e + 1], s_rho[e - 1]);
-        grx = FORCE == 0 ? grad_d1q3(s_rho[e + 1], s_rho[e - 1]) : vc<float2>(0.0);
-        gry = vc<float2>(0.0);
-        gpx = v_mul(phi_diff2(phi_at(m + 1), phi_at(m - 1)), vs(P.gkt2_f, rho));
-        gpy = vc<float2>(0.0);
-    } else {
-        const Nbr9<float2> nb = nbr9(s_rho + e, EX);
-        lap = lap_d2q9(nb);
-        if constexpr (FORCE == 0) grad_d2q9(nb, grx, gry);
-        else grx = gry = vc<float2>(0.0);
-        grad_d2q9_diff(phi_diff2(phi_at(m + 1), phi_at(m - 1)), phi_diff2(phi_at(m + MX), phi_at(m - MX)),
-                       phi_diff2(phi_at(m + MX + 1), phi_at(m - MX - 1)),  // NE - SW
-                       phi_diff2(phi_at(m - MX + 1), phi_at(m + MX - 1)),  // SE - NW
-                       vs(P.gkt3_f, rho), vs(P.gkt12_f, rho), gpx, gpy);
-    }
-    float2 gr[Q], post[Q];
+    float2 rho[NP], lap[NP], grx[NP], gry[NP], gpx[NP], gpy[NP];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        if constexpr (STAGE) gr[i] = s_g[i][tid];
-        else gr[i] = gk[i];
+    for (int q = 0; q < NP; ++q) {
+        const float2 *sr = s_rho[q];
+        const PT *sp = s_phi[q];
+        auto phi_at = [&](int k) {
+            if constexpr (MU == MU_DF) {
+                const float4 t = sp[k];
+                return DF<float2>{make_float2(t.x, t.y), make_float2(t.z, t.w)};
+            } else {
+                return sp[k];
+            }
+        };
+        rho[q] = sr[e];
+        if constexpr (LAT == 1) {
+            lap[q] = lap_d1q3(rho[q], sr[e + 1], sr[e - 1]);
+            grx[q] = FORCE == 0 ? grad_d1q3(sr[e + 1], sr[e - 1]) : vc<float2>(0.0);
+            gry[q] = vc<float2>(0.0);
+            gpx[q] = v_mul(phi_diff2(phi_at(m + 1), phi_at(m - 1)), vs(P.gkt2_f, rho[q]));
+            gpy[q] = vc<float2>(0.0);
+        } else {
+            const Nbr9<float2> nb = nbr9(sr + e, EX);
+            lap[q] = lap_d2q9(nb);
+            if constexpr (FORCE == 0) grad_d2q9(nb, grx[q], gry[q]);
+            else grx[q] = gry[q] = vc<float2>(0.0);
+            grad_d2q9_diff(phi_diff2(phi_at(m + 1), phi_at(m - 1)), phi_diff2(phi_at(m + MX), phi_at(m - MX)),
+                           phi_diff2(phi_at(m + MX + 1), phi_at(m - MX - 1)),  // NE - SW
+                           phi_diff2(phi_at(m - MX + 1), phi_at(m + MX - 1)),  // SE - NW
+                           vs(P.gkt3_f, rho[q]), vs(P.gkt12_f, rho[q]), gpx[q], gpy[q]);
+        }
     }
-    collide_pair<LAT, FORCE>(rho, lap, gpx, gpy, grx, gry, jx, jy, P, gr, post);
+    float2 gr[NP][Q], post[NP][Q];
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if constexpr (STAGE) gr[q][i] = s_g[i][tid];
+            else gr[q][i] = gk[q][i];
+        }
+    collide_pairs<LAT, NP, FORCE>(rho, lap, gpx, gpy, grx, gry, jx, jy, P, gr, post);
 
     // push streaming to the periodic neighbours
     const int xe = small ? wrap(x + 1, nx) : (x + 1 == nx ? 0 : x + 1);
@@ -831,8 +954,11 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
         const int dx = cx == 1 ? xe : (cx == -1 ? xw : x);
         const int dy = cy == 1 ? yn : (cy == -1 ? ys : y);
         float *dst = fout + (size_t)i * plane + (size_t)dy * nx + dx;
-        dst[0] = post[i].x;
-        dst[cq] = post[i].y;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            dst[2 * q * cq] = post[q][i].x;
+            dst[(2 * q + 1) * cq] = post[q][i].y;
+        }
     }
 }
 
@@ -840,8 +966,8 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
 template <int LAT, int N, int TX, int TY, class S, class R, int FORCE, int MU>
 __device__ __forceinline__ void step_tile(const S *__restrict__ fin, S *__restrict__ fout, const DevParams &P,
                                           int x0, int y0) {
-    if constexpr (N == 2 && sizeof(S) == 4 && sizeof(R) == 4 && (MU == MU_DF || MU == MU_F32)) {
-        step_tile_pair<LAT, TX, TY, FORCE, MU>(fin, fout, P, x0, y0);
+    if constexpr (N % 2 == 0 && sizeof(S) == 4 && sizeof(R) == 4 && (MU == MU_DF || MU == MU_F32)) {
+        step_tile_pair<LAT, N / 2, TX, TY, FORCE, MU>(fin, fout, P, x0, y0);
     } else {
     using L = Lat<LAT>;
     using G = TileGeom<LAT, TX, TY>;
