@@ -71,10 +71,10 @@ def parse(argv=None):
 # value holds for the kernel sources whose digest is recorded with it and is reported as
 # null once they change.
 KERNEL_SOURCES = ("lb_kernels.cuh", "lb_lane.cuh", "lb_mu.cuh", "lb_tu.cuh", "lb_launch.cuh", "lb_d2q9_df.cu")
-TRAFFIC = {"fp32_dfmu": {"digest": "0ee2b91ec163041d2b6bfd1bda5b445859ae3b5a9d738645f0a2dd3a141661bf",
-                         "bytes": 107706368, "warp_instructions": 29409280, "issue_active": 0.568,
+TRAFFIC = {"fp32_dfmu": {"digest": "28f0c0ca42a9c5ee8d984f640fd9d5bd5613733efd9225a5655563439f8be7b4",
+                         "bytes": 108212224, "warp_instructions": 29409280, "issue_active": 0.578,
                          "fma_pipe_active": 0.502,
-                         "stalls_per_issue": {"barrier": 3.18, "not_selected": 2.53, "long_scoreboard": 2.48,
+                         "stalls_per_issue": {"barrier": 3.15, "not_selected": 2.51, "long_scoreboard": 2.47,
                                               "math_pipe_throttle": 2.09, "mio_throttle": 1.21},
                          "profile": "profiles/lb_step_kernel_fp32_dfmu_c2_1024.md"}}
 # instruction issue peak of the GPU: 152 SMs x 4 schedulers x 2.07 GHz (one warp instruction
