@@ -71,7 +71,7 @@ def parse(argv=None):
 # value holds for the kernel sources whose digest is recorded with it and is reported as
 # null once they change.
 KERNEL_SOURCES = ("lb_kernels.cuh", "lb_lane.cuh", "lb_mu.cuh", "lb_tu.cuh", "lb_launch.cuh", "lb_d2q9_df.cu")
-TRAFFIC = {"fp32_dfmu": {"digest": "28f0c0ca42a9c5ee8d984f640fd9d5bd5613733efd9225a5655563439f8be7b4",
+TRAFFIC = {"fp32_dfmu": {"digest": "cff1792257b054d114d15bebdcecea016c562078e0e2c4ea5082340d1dc23eac",
                          "bytes": 108212224, "warp_instructions": 29409280, "issue_active": 0.578,
                          "fma_pipe_active": 0.502,
                          "stalls_per_issue": {"barrier": 3.15, "not_selected": 2.51, "long_scoreboard": 2.47,

@@ -48,7 +48,6 @@ __global__ void __launch_bounds__(RESIDENT_THREADS)
     lb_d1q3_resident_kernel(const S *__restrict__ pool_in, S *__restrict__ pool_out,
                             const DevParams *__restrict__ runs, const size_t *__restrict__ offsets,
                             const int *__restrict__ run_ids, int nsteps) {
-    using L1 = Lat<1>;
     using MT = typename MuStore<MU>::T;
     constexpr int Q = 3;
     constexpr int NT = RESIDENT_THREADS;

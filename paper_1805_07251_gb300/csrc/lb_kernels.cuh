@@ -61,10 +61,6 @@ __device__ __forceinline__ double pv<double>(double d, float) { return d; }
 template <>
 __device__ __forceinline__ float pv<float>(double, float f) { return f; }
 
-// 1/x in the compute type: exact division in FP64, MUFU reciprocal in FP32
-__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
-
 // periodic wrap of g in [-n, 2n)
 __device__ __forceinline__ int wrap1(int g, int n) { return g < 0 ? g + n : (g >= n ? g - n : g); }
 

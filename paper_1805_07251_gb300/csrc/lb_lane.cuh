@@ -35,10 +35,6 @@ __device__ __forceinline__ float2 v_sub(float2 a, float2 b) { return __fadd2_rn(
 __device__ __forceinline__ float2 v_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 v_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// element type of a lane type
-template <class V> struct LaneElem { using T = V; };
-template <> struct LaneElem<float2> { using T = float; };
-
 // a constant in every lane (rounded to the element type)
 template <class V> __device__ __forceinline__ V vc(double c);
 template <> __device__ __forceinline__ double vc<double>(double c) { return c; }

@@ -83,8 +83,6 @@ __device__ __forceinline__ df df_from_double(double v) {
 
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 
-__device__ __forceinline__ float df_to_float(df a) { return __fadd_rn(a.hi, a.lo); }
-
 // 1/a for a positive df a (possibly unnormalised).  y ~ 1/a.hi from the MUFU approximation
 // and one Newton step lies within an ulp of 1/a.hi, so the residual 1 - a.hi y is exact in
 // one fused multiply-add; with e = 1 - a y, 1/a = y (1 + e + e^2 + ...), and the e^3 term
