@@ -2,7 +2,8 @@
  * lbvdw_selftest.h -- self-test entry points of the lbvdw library (not part of the
  * lattice Boltzmann step).  lb_selftest_log exposes the two logarithms the
  * chemical-potential stage uses on GB300 so that tests can compare them with CUDA's
- * double-precision log on the same device:
+ * double-precision log on the same device (lb_selftest_recip does the same for its
+ * double-float reciprocal):
  *   - the table-driven FP64 logarithm of the LB_FP32_MIXED path;
  *   - the double-float logarithm of the LB_FP32_DFMU path.
  * The chemical potential that needs these logarithms is Eq. discreteChemicalPotential
@@ -27,6 +28,15 @@ extern "C" {
  * LB_E_NOMEM, LB_E_CUDA. */
 lb_status lb_selftest_log(int32_t device, const double *x, int64_t n, double *out_tbl, double *out_df,
                           double *out_ref);
+
+/* For n host values x[k] > 0 (normal, finite, x[k] and 1/x[k] within the float range)
+ * compute on device `device` out_df[k] = 1/x[k] by the double-float reciprocal of the
+ * LB_FP32_DFMU chemical potential (the 1/eta = 1/(1 - sum_c b^c rho^c) of Eq.
+ * discreteChemicalPotential), x first rounded to a double-float pair and the result
+ * returned as hi + lo in double.  Host arrays of n doubles owned by the caller; allocates
+ * and frees its own device scratch; synchronous.  Errors: LB_E_INVALID (NULL pointer,
+ * n < 1), LB_E_NOMEM, LB_E_CUDA. */
+lb_status lb_selftest_recip(int32_t device, const double *x, int64_t n, double *out_df);
 
 /* The bounded wait that the streaming-strip kernel (LB_KERNEL_STRIPS) applies to its
  * bulk-copy barriers, run on one CTA of 64 threads on device `device` against an mbarrier

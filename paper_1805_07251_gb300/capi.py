@@ -101,6 +101,7 @@ def load():
         "lb_status_str": (ctypes.c_char_p, [ctypes.c_int]),
         "lb_last_error": (ctypes.c_char_p, [C]),
         "lb_selftest_log": (ctypes.c_int, [ctypes.c_int32, _DP, ctypes.c_int64, _DP, _DP, _DP]),
+        "lb_selftest_recip": (ctypes.c_int, [ctypes.c_int32, _DP, ctypes.c_int64, _DP]),
         "lb_selftest_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.c_uint32, ctypes.c_int32,
                                             ctypes.POINTER(ctypes.c_uint32)]),
         "lb_free_energy_noalloc": (ctypes.c_int, [P, C, C]),
@@ -242,6 +243,16 @@ def lb_selftest_log(device, x):
     rc = load().lb_selftest_log(int(device), _dp(x), x.size, _dp(o[0]), _dp(o[1]), _dp(o[2]))
     if rc != LB_OK:
         raise LBError(rc, "lb_selftest_log")
+    return o
+
+
+def lb_selftest_recip(device, x):
+    """The double-float reciprocal of the chemical potential (1/eta) of x on the device."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    o = np.empty_like(x)
+    rc = load().lb_selftest_recip(int(device), _dp(x), x.size, _dp(o))
+    if rc != LB_OK:
+        raise LBError(rc, "lb_selftest_recip")
     return o
 
 

@@ -23,6 +23,13 @@ __global__ void selftest_log_kernel(const double *x, long long n, const lbvdw::L
     o_ref[k] = log(v);
 }
 
+// 1/x through the double-float reciprocal of the chemical-potential stage (1/eta)
+__global__ void selftest_recip_kernel(const double *x, long long n, double *o_df) {
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    o_df[k] = lbvdw::df_to_double(lbvdw::df_recip(lbvdw::df_from_double(x[k])));
+}
+
 // The bounded mbarrier wait of the streaming-strip kernel on a barrier that completes
 // (thread 0 arrives) or never does (nobody arrives): the wait must end either way and
 // report the second case in the flag.
@@ -92,5 +99,28 @@ extern "C" lb_status lb_selftest_log(int32_t device, const double *x, int64_t n,
     }
     cudaFree(d);
     cudaFree(tb);
+    return st;
+}
+
+extern "C" lb_status lb_selftest_recip(int32_t device, const double *x, int64_t n, double *out_df) {
+    if (!x || !out_df || n < 1) return LB_E_INVALID;
+    if (cudaSetDevice(device) != cudaSuccess) return LB_E_CUDA;
+    double *d = nullptr;
+    size_t bytes = sizeof(double) * (size_t)n;
+    if (cudaMalloc(&d, 2 * bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return LB_E_NOMEM;
+    }
+    lb_status st = LB_OK;
+    if (cudaMemcpy(d, x, bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        st = LB_E_CUDA;
+    } else {
+        unsigned grid = (unsigned)((n + 255) / 256);
+        selftest_recip_kernel<<<grid, 256>>>(d, n, d + n);
+        if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+            cudaMemcpy(out_df, d + n, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = LB_E_CUDA;
+    }
+    cudaFree(d);
     return st;
 }

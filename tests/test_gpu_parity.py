@@ -306,6 +306,19 @@ def test_chemical_potential_logarithms(gpu_lib):
     assert np.max(np.abs(dfl - ref) / scale) < 2.0 ** -43
 
 
+def test_double_float_reciprocal(gpu_lib):
+    # 1/eta of the double-float chemical potential (MUFU seed, one Newton step, exact FMA
+    # residual, second-order correction) against the FP64 quotient: relative error at the
+    # df precision, over eta's range (0, 1] and beyond
+    from paper_1805_07251_gb300 import capi
+
+    r = np.random.default_rng(5)
+    x = np.concatenate([r.uniform(1e-3, 1.0, 40000), np.exp(r.uniform(-20, 20, 20000)),
+                        [1.0, 0.5, 2.0, 1 - 2.0 ** -24, 1 + 2.0 ** -23, 0.75, 1.0 / 3.0]])
+    inv = capi.lb_selftest_recip(0, x)
+    assert np.max(np.abs(inv * x - 1.0)) < 2.0 ** -44
+
+
 @pytest.mark.parametrize("precision", ["fp32_mixed", "fp32_dfmu", "fp32"])
 def test_fp32_one_phase_within_1e5_of_fp64_oracle(gpu_lib, precision):
     p = lbinputs.base_params("c2")
