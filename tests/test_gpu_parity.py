@@ -200,6 +200,35 @@ def test_fp64_full_size_config2_sampled_one_step(gpu_lib):
         assert np.max(np.abs(j_g[:, :, y, x] - jo[:, :, 4, 4])) < 1e-13
 
 
+@pytest.mark.parametrize("config,precision,bar", [("c2", "fp32_dfmu", 2e-6), ("c4", "fp32_dfmu", 2e-6)])
+def test_fp32_full_size_sampled_one_step(gpu_lib, config, precision, bar):
+    # the benchmark's FP32 launch configurations at full size (1024^2 two components,
+    # 2048^2 four components, 32x8 tiles in lane pairs): one GPU step against the FP64
+    # oracle's step on 9 x 9 periodic windows around sampled nodes.  The GPU starts from
+    # FP32-stored deviations and steps in FP32, so the bar is FP32 rounding, not 1e-13.
+    p = lbinputs.base_params(config)
+    sim, _ = make_pair(p, precision=precision)
+    assert sim.kernel == ("tiles", (32, 8))
+    rho = lbinputs.fields(config)
+    N, ny, nx = rho.shape
+    sim.init(rho)
+    sim.step(1)
+    r_g, j_g = sim.moments()
+    r = np.random.default_rng(78)
+    kw = lbinputs.lib_kwargs(p)
+    win = oracle.Lattice("D2Q9", 9, 9, N, kw["tau"], kw["kT"], kw["gamma_mu"], kw["a"], kw["kappa"],
+                         kw["lam"], kw["b"])
+    pts = [(0, 0), (ny - 1, nx - 1), (ny // 2, 0), (0, nx - 7)]
+    pts += [(int(r.integers(0, ny)), int(r.integers(0, nx))) for _ in range(30)]
+    worst = 0.0
+    for (y, x) in pts:
+        ys = (np.arange(-4, 5) + y) % ny
+        xs = (np.arange(-4, 5) + x) % nx
+        ro, jo = win.moments(win.run(win.equilibrium(rho[:, ys][:, :, xs]), 1))
+        worst = max(worst, np.max(np.abs(r_g[:, y, x] - ro[:, 4, 4])), np.max(np.abs(j_g[:, :, y, x] - jo[:, :, 4, 4])))
+    assert worst < bar, worst
+
+
 def test_free_energy_diagnostic_matches_oracle(gpu_lib):
     p = lbinputs.base_params("c2")
     sim, orc = make_pair(p, nx=64, ny=50)
