@@ -228,6 +228,30 @@ void make_dev_params(const lb_params &p, DevParams &d, unsigned *err, const LogT
     d.ln2_lo_f = (float)(ln2 - (long double)d.ln2_hi_f);
 }
 
+// Per-block sums of the N density fields rho[c][s] (s < n) in a fixed order; the partials
+// then go through lb_diag_final_kernel, so the means are deterministic.
+template <int N>
+__global__ void __launch_bounds__(DIAG_THREADS)
+    lb_field_sum_kernel(const double *__restrict__ rho, size_t n, double *__restrict__ partial) {
+    double acc[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) acc[k] = 0.0;
+    for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < n; s += (size_t)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int k = 0; k < N; ++k) acc[k] += rho[(size_t)k * n + s];
+    block_sum<N>(acc, partial + (size_t)blockIdx.x * N);
+}
+
+template <int N>
+static cudaError_t field_sums(const double *rho, size_t n, double *partial, int nparts, double *out,
+                              cudaStream_t st) {
+    lb_field_sum_kernel<N><<<nparts, DIAG_THREADS, 0, st>>>(rho, n, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    lb_diag_final_kernel<N><<<1, DIAG_THREADS, 0, st>>>(partial, nparts, out);
+    return cudaGetLastError();
+}
+
 }  // namespace lbvdw
 
 extern "C" {
@@ -375,15 +399,17 @@ static lb_status device_mean(lb_ctx *c, const double *rho_dev, double *mean) {
     if (c->p.precision != LB_FP64)
         for (int k = 0; k < N; ++k) need_mean = need_mean || !(c->p.rho_ref[k] > 0.0);
     if (!need_mean) return LB_OK;
-    if (rho_dev != c->rho)
-        LB_CUDA(c, cudaMemcpyAsync(c->rho, rho_dev, sizeof(double) * N * c->n, cudaMemcpyDeviceToDevice, c->stream));
-    LB_CUDA(c, cudaMemsetAsync(c->mom, 0, sizeof(double) * N * c->D * c->n, c->stream));
-    FieldLaunch a = field_args(c);
-    cudaError_t e = run_field(c, 2, a);
-    if (e != cudaSuccess) return cuda_fail(c, e, "diag kernel");
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (N) {
+        case 1: e = field_sums<1>(rho_dev, c->n, c->partial, c->nparts, c->diag, c->stream); break;
+        case 2: e = field_sums<2>(rho_dev, c->n, c->partial, c->nparts, c->diag, c->stream); break;
+        case 3: e = field_sums<3>(rho_dev, c->n, c->partial, c->nparts, c->diag, c->stream); break;
+        case 4: e = field_sums<4>(rho_dev, c->n, c->partial, c->nparts, c->diag, c->stream); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "field sum kernel");
     c->launches += 2;
-    double h[7];
-    LB_CUDA(c, cudaMemcpyAsync(h, c->diag, sizeof(double) * (N + 3), cudaMemcpyDeviceToHost, c->stream));
+    double h[4];
+    LB_CUDA(c, cudaMemcpyAsync(h, c->diag, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(c, cudaStreamSynchronize(c->stream));
     for (int k = 0; k < N; ++k) mean[k] = h[k] / (double)c->n;
     return LB_OK;
