@@ -868,7 +868,8 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
 
     // ---- phase 2: phi on tile + 1 ring --------------------------------------------
     unsigned bad = 0;
-    for (int k = tid; k < MX * MY; k += NT) {
+    // phi at mu node k (into s_phi when store); false outside the domain
+    auto mu_at = [&](int k, bool store) {
         const int mx = k % MX, my = k / MX;
         const int e = (my + HY) * EX + mx + 1;
         float2 r[NP], lp[NP], lin[NP];
@@ -879,17 +880,38 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
             else lp[q] = lap_d2q9(nbr9(s_rho[q] + e, EX));
         }
         lin_pairs<NP>(r, lp, P, lin);
+        bool ok;
         if constexpr (MU == MU_DF) {
             DF<float2> ph[NP];
-            if (!mu_pairs_df<NP, FORCE>(r, lin, P, reinterpret_cast<const float4 *>(s_tbl), ph)) bad = 1;
+            ok = mu_pairs_df<NP, FORCE>(r, lin, P, reinterpret_cast<const float4 *>(s_tbl), ph);
 #pragma unroll
-            for (int q = 0; q < NP; ++q) s_phi[q][k] = make_float4(ph[q].hi.x, ph[q].hi.y, ph[q].lo.x, ph[q].lo.y);
+            for (int q = 0; q < NP; ++q)
+                if (store) s_phi[q][k] = make_float4(ph[q].hi.x, ph[q].hi.y, ph[q].lo.x, ph[q].lo.y);
         } else {
             float2 ph[NP];
-            if (!mu_pairs_f32<NP, FORCE>(r, lin, P, ph)) bad = 1;
+            ok = mu_pairs_f32<NP, FORCE>(r, lin, P, ph);
 #pragma unroll
-            for (int q = 0; q < NP; ++q) s_phi[q][k] = ph[q];
+            for (int q = 0; q < NP; ++q)
+                if (store) s_phi[q][k] = ph[q];
         }
+        return ok || !store;
+    };
+    if constexpr (MX * MY > NT && MX * MY <= 2 * NT) {
+        // warps with second-round mu nodes evaluate both of a thread's nodes in one
+        // straight-line stream, two independent dependency chains (the second round otherwise
+        // runs alone on a third of the warps); a lane without a second node repeats its first
+        // without storing it
+        if ((tid & ~31) + NT < MX * MY) {
+            const bool has2 = tid + NT < MX * MY;
+            const bool ok1 = mu_at(tid, true);
+            const bool ok2 = mu_at(has2 ? tid + NT : tid, has2);
+            if (!(ok1 && ok2)) bad = 1;
+        } else if (!mu_at(tid, true)) {
+            bad = 1;
+        }
+    } else {
+        for (int k = tid; k < MX * MY; k += NT)
+            if (!mu_at(k, true)) bad = 1;
     }
     __syncthreads();
     if (bad) atomicOr(P.err, ERR_DOMAIN);
