@@ -71,11 +71,11 @@ def parse(argv=None):
 # value holds for the kernel sources whose digest is recorded with it and is reported as
 # null once they change.
 KERNEL_SOURCES = ("lb_kernels.cuh", "lb_lane.cuh", "lb_mu.cuh", "lb_tu.cuh", "lb_launch.cuh", "lb_d2q9_df.cu")
-TRAFFIC = {"fp32_dfmu": {"digest": "cff1792257b054d114d15bebdcecea016c562078e0e2c4ea5082340d1dc23eac",
-                         "bytes": 108212224, "warp_instructions": 29409280, "issue_active": 0.578,
-                         "fma_pipe_active": 0.502,
-                         "stalls_per_issue": {"barrier": 3.15, "not_selected": 2.51, "long_scoreboard": 2.47,
-                                              "math_pipe_throttle": 2.09, "mio_throttle": 1.21},
+TRAFFIC = {"fp32_dfmu": {"digest": "15d44b628b0c3c84cfc97e51269edaf91bfcfdbb801f1828ea2926e9bfbf22e0",
+                         "bytes": 107393280, "warp_instructions": 28700672, "issue_active": 0.577,
+                         "fma_pipe_active": 0.509,
+                         "stalls_per_issue": {"barrier": 3.11, "not_selected": 2.52, "long_scoreboard": 2.50,
+                                              "math_pipe_throttle": 2.14, "mio_throttle": 1.19},
                          "profile": "profiles/lb_step_kernel_fp32_dfmu_c2_1024.md"}}
 # instruction issue peak of the GPU: 152 SMs x 4 schedulers x 2.07 GHz (one warp instruction
 # per scheduler per cycle)

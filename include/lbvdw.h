@@ -94,7 +94,7 @@ typedef enum { LB_FORCE_LOG = 0, LB_FORCE_NID = 1 } lb_force_method;
  *                     mbarrier completion) while the current rows are collided.
  *                     Needs nx % tile_x == 0 and ny % tile_y == 0, with
  *                     (tile_x, tile_y) = (32, 8) for 1-2 components, (32, 4) for 3-4.
- *   LB_KERNEL_AUTO    tiles (measured faster on GB300: 43.8k against 27.7k component-
+ *   LB_KERNEL_AUTO    tiles (measured faster on GB300: 44.5k against 27.8k component-
  *                     MLUPS for 2 components at 1024^2; the strips' shared-memory
  *                     staging leaves two CTAs, 18 warps, per SM). */
 typedef enum { LB_KERNEL_AUTO = 0, LB_KERNEL_TILES = 1, LB_KERNEL_STRIPS = 2 } lb_kernel_kind;
