@@ -14,6 +14,9 @@
 // FP64 path, so g = f there).  Compute type R is double in the FP64 path and float in
 // the mixed paths, where eta, 1/eta, the logarithms and the differences of mu are
 // carried in FP64 (MU_TBL) or in double-float arithmetic (MU_DF), see lb_mu.cuh.
+// The per-node arithmetic is written over lane types (lb_lane.cuh): an even number of
+// FP32 components runs as float2 pairs on the packed FP32x2 instructions
+// (step_tile_pair), bitwise equal to one component at a time.
 #pragma once
 #include <cstdint>
 #include <type_traits>
