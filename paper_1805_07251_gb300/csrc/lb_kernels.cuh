@@ -795,6 +795,12 @@ struct TileGeom {
     }
 };
 
+// Whether a step runs in lane pairs: an even number of FP32 components, FP32-class mu.
+template <int N, class S, class R, int MU>
+struct PairPath {
+    static constexpr bool value = N % 2 == 0 && sizeof(S) == 4 && sizeof(R) == 4 && (MU == MU_DF || MU == MU_F32);
+};
+
 // The fused step, FP32 components in lane pairs (NP pairs: components 2q and 2q+1 in pair q):
 // every per-node quantity of a pair lives in one register pair (densities, momenta, mu,
 // forces, populations) and is computed by the packed FP32x2 instructions; shared memory
@@ -810,10 +816,13 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
     using PT = typename std::conditional<MU == MU_DF, float4, float2>::type;  // phi pair: (hi, hi, lo, lo) / (x, y)
 
     // the node's own populations wait in shared memory between phases 1 and 3 (one pair,
-    // tiles of up to 256 threads), else in registers
+    // tiles of up to 256 threads), or are read again from global memory (the L2) in phase 3
+    // (two pairs: holding them would cost 36 registers and half the resident CTAs), else
+    // they wait in registers
     constexpr bool STAGE = NP == 1 && NT <= 256;
+    constexpr bool RELOAD = NP > 1;
     __shared__ float2 s_g[STAGE ? Q : 1][STAGE ? NT : 1];
-    float2 gk[STAGE ? 1 : NP][STAGE ? 1 : Q];
+    float2 gk[STAGE || RELOAD ? 1 : NP][STAGE || RELOAD ? 1 : Q];
     __shared__ float2 s_rho[NP][G::EY * EX];
     __shared__ PT s_phi[NP][MY * MX];
     __shared__ __align__(16) float s_tbl[TblWords<MU>::value];
@@ -845,7 +854,7 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
             for (int i = 0; i < Q; ++i) {
                 gv[i] = make_float2(sq[(size_t)i * plane], sq[cq + (size_t)i * plane]);
                 if constexpr (STAGE) s_g[i][tid] = gv[i];
-                else gk[q][i] = gv[i];
+                else if constexpr (!RELOAD) gk[q][i] = gv[i];
             }
             moments_lane<LAT>(gv, acc, jx[q], jy[q]);
             s_rho[q][(ty + 2 * HY) * EX + tx + 2] = v_add(rref[q], acc);
@@ -960,7 +969,10 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             if constexpr (STAGE) gr[q][i] = s_g[i][tid];
-            else gr[q][i] = gk[q][i];
+            else if constexpr (RELOAD) {
+                const float *sq = fin + (size_t)y * nx + x + 2 * q * cq;
+                gr[q][i] = make_float2(sq[(size_t)i * plane], sq[cq + (size_t)i * plane]);
+            } else gr[q][i] = gk[q][i];
         }
     collide_pairs<LAT, NP, FORCE>(rho, lap, gpx, gpy, grx, gry, jx, jy, P, gr, post);
 
@@ -987,7 +999,7 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
 template <int LAT, int N, int TX, int TY, class S, class R, int FORCE, int MU>
 __device__ __forceinline__ void step_tile(const S *__restrict__ fin, S *__restrict__ fout, const DevParams &P,
                                           int x0, int y0) {
-    if constexpr (N % 2 == 0 && sizeof(S) == 4 && sizeof(R) == 4 && (MU == MU_DF || MU == MU_F32)) {
+    if constexpr (PairPath<N, S, R, MU>::value) {
         step_tile_pair<LAT, N / 2, TX, TY, FORCE, MU>(fin, fout, P, x0, y0);
     } else {
     using L = Lat<LAT>;
@@ -1121,15 +1133,16 @@ __device__ __forceinline__ void step_tile(const S *__restrict__ fin, S *__restri
 }
 
 // FP32 storage, 256-thread tiles: ask for five resident CTAs per SM with up to two
-// components (48 registers), two with three or four (128 registers); more resident warps
-// hide the barrier waits between the phases.
-template <class S, int N, int NT>
+// components (48 registers); four for four components in lane pairs (64 registers: their
+// populations are read again in phase 3 rather than held); two otherwise (128 registers).
+// More resident warps hide the barrier waits between the phases.
+template <class S, int N, int NT, bool PAIR>
 struct MinBlocks {
-    static constexpr int value = (sizeof(S) == 4 && NT == 256) ? (N <= 2 ? 5 : 2) : 1;
+    static constexpr int value = (sizeof(S) == 4 && NT == 256) ? (N <= 2 ? 5 : (PAIR && N == 4 ? 4 : 2)) : 1;
 };
 
 template <int LAT, int N, int TX, int TY, class S, class R, int FORCE, int MU>
-__global__ void __launch_bounds__(TX *TY, MinBlocks<S, N, TX * TY>::value)
+__global__ void __launch_bounds__(TX *TY, MinBlocks<S, N, TX * TY, PairPath<N, S, R, MU>::value>::value)
     lb_step_kernel(const S *__restrict__ fin, S *__restrict__ fout, DevParams P) {
     step_tile<LAT, N, TX, TY, S, R, FORCE, MU>(fin, fout, P, blockIdx.x * TX, blockIdx.y * TY);
 }
