@@ -22,7 +22,7 @@ struct BatchTile {
 };
 
 template <int N, int TX, int TY, class S, class R, int FORCE, int MU>
-__global__ void __launch_bounds__(TX *TY)
+__global__ void __launch_bounds__(TX *TY, MinBlocks<S, N, TX * TY, PairPath<N, S, R, MU>::value>::value)
     lb_batch_tile_kernel(const S *__restrict__ pool_in, S *__restrict__ pool_out, const DevParams *__restrict__ runs,
                          const size_t *__restrict__ offsets, const BatchTile *__restrict__ tiles) {
     const BatchTile t = tiles[blockIdx.x];
