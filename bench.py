@@ -192,13 +192,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline_oracle(kw, rho_full, nx, steps):
-    """Time the CPU oracle (as it stands) on an nx x nx sample of the same recipe."""
-    import numpy as np
+def cpu_model():
+    """The host CPU's model name (lscpu), for the CPU-baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
 
+    return platform.processor() or platform.machine()
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def cpu_baseline_oracle(kw, nx, steps, threads):
+    """Time the CPU oracle (as it stands, OpenMP over rows with ``threads`` threads) on an
+    nx x nx sample of the same recipe; returns (component-MLUPS, seconds, threads used)."""
     import lbinputs
     import oracle
 
+    used = oracle.set_threads(threads)
     rho = lbinputs.fields(WORKLOAD, nx=nx, ny=nx)
     L = oracle.Lattice(kw["lattice"], nx, nx, kw["ncomp"], kw["tau"], kw["kT"], kw["gamma_mu"], kw["a"],
                        kw["kappa"], kw["lam"], kw["b"])
@@ -206,36 +224,7 @@ def cpu_baseline_oracle(kw, rho_full, nx, steps):
     t0 = time.perf_counter()
     L.run(f, steps)
     dt = time.perf_counter() - t0
-    value = kw["ncomp"] * nx * nx * steps / dt / 1e6
-    del np
-    return value, dt
-
-
-def _oracle_sample(job):
-    """One process of the all-cores CPU baseline: the oracle on its own nx x nx sample."""
-    kw, nx, steps = job
-    import lbinputs
-    import oracle
-
-    rho = lbinputs.fields(WORKLOAD, nx=nx, ny=nx)
-    L = oracle.Lattice(kw["lattice"], nx, nx, kw["ncomp"], kw["tau"], kw["kT"], kw["gamma_mu"], kw["a"],
-                       kw["kappa"], kw["lam"], kw["b"])
-    f = L.equilibrium(rho)
-    t0 = time.perf_counter()
-    L.run(f, steps)
-    return time.perf_counter() - t0
-
-
-def cpu_baseline_all_cores(kw, nx, steps):
-    """The same oracle sample run by one process per host core at once (spawned processes:
-    the parent has a CUDA context); aggregate component-MLUPS over the slowest process."""
-    import multiprocessing as mp
-
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    kwl = {k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in kw.items()}
-    with mp.get_context("spawn").Pool(cores) as pool:
-        dts = pool.map(_oracle_sample, [(kwl, nx, steps)] * cores)
-    return cores * kw["ncomp"] * nx * nx * steps / max(dts) / 1e6, cores, max(dts)
+    return kw["ncomp"] * nx * nx * steps / dt / 1e6, dt, used
 
 
 def run_reference(args):
@@ -250,6 +239,7 @@ def run_reference(args):
     p = lbinputs.base_params(WORKLOAD)
     kw = lbinputs.lib_kwargs(p)
     rho = lbinputs.fields(WORKLOAD)
+    threads = oracle.set_threads(host_cores())
     L = oracle.Lattice(kw["lattice"], kw["nx"], kw["ny"], kw["ncomp"], kw["tau"], kw["kT"], kw["gamma_mu"], kw["a"],
                        kw["kappa"], kw["lam"], kw["b"])
     f = L.equilibrium(rho)
@@ -265,8 +255,9 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "D2Q9, 2 components, 1024x1024 periodic, spinodal mixture (c2)",
                    "nodes": nodes, "ncomp": kw["ncomp"]},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"full 1024x1024 lattice, {args.steps} oracle timesteps after {args.warmup} warm-up"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu": cpu_model(),
+                         "sample": f"full 1024x1024 lattice, {args.steps} oracle timesteps after {args.warmup} "
+                                   f"warm-up, OpenMP over rows with {threads} threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -314,8 +305,10 @@ def time_c4(torch, dev, precision, steps, warmup):
     one-fluid critical temperature.  Times `steps` timesteps, then runs on towards the
     configuration's 5000 steps in chunks of 50, reporting the per-component mass drift at
     the last chunk that ended inside the density domain and the step at which the run left
-    it (this deep quench drives some node's density to zero after a few hundred steps at
-    every gamma_mu tried, in FP64 as in FP32; see the design notes)."""
+    it.  This deep quench drives some node's density to zero after a number of steps
+    proportional to 1/gamma_mu for every gamma_mu tried, in FP64 as in FP32: the mean's
+    unstable direction has every component of one sign, so total-density waves grow
+    until a gas node empties."""
     import numpy as np
 
     import lbinputs
@@ -578,6 +571,17 @@ def main():
         if sampler:
             clocks = sampler.stop()
         launches = sim.launches - l0
+        nf_ms = None
+        if precision == HEAD:
+            # the same K steps back to back between two events, no L2 flush in between
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            sim.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            nf_ms = max_over_ranks(dist, e0.elapsed_time(e1), dev) / args.steps
+            launches += args.steps
         per = [a.elapsed_time(b) for a, b in ev]
         total_ms = max_over_ranks(dist, float(sum(per)), dev)
         kind, tile = sim.kernel
@@ -587,7 +591,7 @@ def main():
         alg_bytes = N * nodes * 9 * 2 * elem
         achieved = alg_bytes / (ms * 1e-3) / 1e9
         results[precision] = dict(value=value, ms=ms, launches=launches, alg_bytes=alg_bytes, achieved=achieved,
-                                  kernel="%s %dx%d" % (kind, tile[0], tile[1]))
+                                  kernel="%s %dx%d" % (kind, tile[0], tile[1]), nf_ms=nf_ms)
         sim.close()
 
     sweep = None
@@ -656,6 +660,20 @@ def main():
                      "limiter": limiter_of(HEAD, head["alg_bytes"], peak_gbs)},
         "gpu_launches": head["launches"],
     }
+    if head.get("nf_ms"):
+        nf = head["nf_ms"]
+        line["no_flush"] = {
+            "value": job_throughput(world, N * nodes, nf * 1e-3), "unit": UNIT, "ms_per_step": nf,
+            "achieved_gbs": head["alg_bytes"] / (nf * 1e-3) / 1e9,
+            "frac": head["alg_bytes"] / (nf * 1e-3) / 1e9 / peak_gbs,
+            "note": "the same K steps back to back between two CUDA events, no L2 flush between them "
+                    "(writes of one step may still drain during the next)"}
+    if "fp32_mixed" in results:
+        fm = results["fp32_mixed"]
+        line["config"]["fp64_mu_path"] = (
+            "FP32 storage with mu in FP64 (the precision split of the method's FP32 variant taken "
+            "literally): %.0f component-MLUPS, %.1f %% of the HBM peak; the headline replaces the FP64 "
+            "mu by double-float (~44-bit) mu on the FP32 pipe" % (fm["value"], 100 * fm["achieved"] / peak_gbs))
     if e2e is not None:
         line["e2e"] = e2e
     if adjoint is not None:
@@ -683,19 +701,17 @@ def main():
     if clocks:
         line["clocks"] = clocks
     if world == 1 and not args.no_cpu_baseline and not args.only:
-        ncb = 256
-        steps_cb = 100
-        v, dt = cpu_baseline_oracle(kw, rho, ncb, steps_cb)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{ncb}x{ncb} lattice of the same recipe, {steps_cb} oracle timesteps "
-                                          f"({dt:.1f} s, single thread)"}
-        try:
-            va, cores, dta = cpu_baseline_all_cores(kw, ncb, steps_cb)
-            line["cpu_baseline"]["all_cores"] = {
-                "value": va, "unit": UNIT, "cores": cores,
-                "sample": f"the same sample in {cores} concurrent oracle processes ({dta:.1f} s for the slowest)"}
-        except Exception as e:  # a host without process spawning still gets the 1-core line
-            line["cpu_baseline"]["all_cores"] = {"error": str(e)[:200]}
+        # the oracle as it stands: OpenMP over rows on every host core (the headline CPU
+        # figure), and one thread on a smaller sample
+        cores = host_cores()
+        va, dta, used = cpu_baseline_oracle(kw, 1024, 10, cores)
+        v1, dt1, _ = cpu_baseline_oracle(kw, 256, 100, 1)
+        line["cpu_baseline"] = {
+            "value": va, "unit": UNIT, "cores": used, "kind": "oracle", "cpu": cpu_model(),
+            "sample": f"full 1024x1024 lattice of the same recipe, 10 oracle timesteps ({dta:.1f} s, "
+                      f"OpenMP over rows, {used} threads)",
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                              "sample": f"256x256 lattice of the same recipe, 100 oracle timesteps ({dt1:.1f} s)"}}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

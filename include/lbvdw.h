@@ -43,6 +43,13 @@
  *     but lb_init_fields*, lb_load_state, lb_last_error and lb_destroy returns LB_E_STATE
  *     until the fields are set again.
  *   - One context must not be used from two host threads at the same time.
+ *   - Each call makes its context's device current while it runs and restores the
+ *     calling thread's current device before returning.
+ *   - Streams: NULL in lb_params.stream is CUDA's legacy default stream (a C ABI has no
+ *     notion of a framework's "current" stream); the Python binding passes PyTorch's
+ *     current stream when the caller names none.
+ *   - Device memory of a context comes from cudaMalloc in lb_create (freed by
+ *     lb_destroy); lb_free_energy_noalloc allocates nothing.
  */
 #ifndef LBVDW_H
 #define LBVDW_H
@@ -194,9 +201,11 @@ lb_status lb_free_energy(lb_ctx *ctx, double *F, double *mass, double *mom_total
  * D2Q9), e.g. a 512 x 512 D2Q9 lattice with two components; larger states are rejected
  * with LB_E_INVALID.  Every call shares the array and it keeps the last call's contents
  * (the error word is cleared at the start of each call); calls that overlap on the GPU
- * race, so serialise them.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current: make it before any stream
- * capture.  Calls no cudaMalloc, cudaFree or allocating library routine.
+ * race, so serialise them.  Each call looks up the array's device address
+ * (cudaGetSymbolAddress, which allocates nothing) with p->device current, so the address
+ * stays right after a device reset; the first call on a device also loads the library's
+ * module there, so make it before any stream capture.  The caller's current device is
+ * restored before returning.  Calls no cudaMalloc, cudaFree or allocating library routine.
  * Errors: LB_E_INVALID, LB_E_CUDA. */
 lb_status lb_free_energy_noalloc(const lb_params *p, const void *f_dev, double *out_dev);
 

@@ -13,13 +13,16 @@ Workloads (the five configurations the library is measured and checked on):
 Seeds: configuration k draws from numpy ``default_rng(1805072510 + k)``; run r
 of the sweep from ``default_rng(1805072600 + r)``.
 
-Readings fixed here (each is stated with its reason in the design notes):
+Readings fixed here, where the workloads leave a choice open (reason with each):
   * kT is a fraction of the van der Waals one-fluid critical temperature at the
     run's mean mole fractions x: theta_cr^mix = 8 (x.a.x) / (27 b.x), the
     single-component relation theta_cr = 8a/(27b) of Sec. II with a and b
-    replaced by their quadratic and linear mole-fraction averages.
-  * kappa^{cc'} = kappa for every pair; lambda^{cc'} = 1 between different
-    components (the paper gives no lambda; equilibrium does not depend on it).
+    replaced by their quadratic and linear mole-fraction averages (the pure-
+    component reading would put the mean states of two workloads in the
+    one-phase region, where nothing separates).
+  * kappa^{cc'} = kappa for every pair (the workloads give one kappa);
+    lambda^{cc'} = 1 between different components (the paper gives no lambda;
+    equilibrium does not depend on it).
   * gamma_mu and the slab width come from ``params.json``, written by
     ``tests/golden/make_config_params.py`` from the oracle (Sec. V rule
     c_s^2 = 1 - 4 kappa rho_l gamma_mu, then a stability pre-scan).

@@ -9,8 +9,9 @@ the bulk thermodynamics (Sec. II) and the coexistence solvers the step is
 pinned against.
 
 The ctypes wrapper below compiles ``lbvdw_oracle.c`` with plain ``gcc -O2``
-(no fast-math, no FMA contraction) on first use, or uses the copy that
-``__graft_entry__.build()`` compiled.
+(no fast-math, no FMA contraction, OpenMP over rows when the compiler has it) on
+first use, or uses the copy that ``__graft_entry__.build()`` compiled.  The
+number of threads never changes a result (``set_threads``).
 """
 from __future__ import annotations
 
@@ -62,7 +63,9 @@ def build(force: bool = False) -> str:
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-ffp-contract=off",
                "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        r = subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True, text=True)
+        if r.returncode != 0:            # no OpenMP runtime: the same code, one thread
+            subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -80,11 +83,18 @@ def _load():
             lib.orc_forces.argtypes = [P, dp, dp, dp]
             lib.orc_equilibrium.argtypes = [P, dp, dp, dp]
             lib.orc_free_energy.argtypes = [P, dp, dp, dp]
+            lib.orc_set_threads.argtypes = [ctypes.c_int]
             for fn in (lib.orc_run, lib.orc_moments, lib.orc_mu, lib.orc_forces,
-                       lib.orc_equilibrium, lib.orc_free_energy):
+                       lib.orc_equilibrium, lib.orc_free_energy, lib.orc_set_threads):
                 fn.restype = ctypes.c_int
             _lib = lib
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads the oracle's stages use (n < 1: leave unchanged); returns the number in
+    effect (1 when built without OpenMP)."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 def _dptr(a):

@@ -21,8 +21,8 @@
  *            Sec. III, BGK collision (Eq. BGKcollisionOperator, single tau)
  *   stage 7  streaming (Eq. LBequation), periodic in every direction
  *
- * Readings of the paper taken here (every one is listed with its reason in the
- * design notes of the repository):
+ * Readings of the paper taken here, where it is silent or its printed signs
+ * disagree with one another (the reason follows each):
  *   - the momentum GAINED by component c is G^c = -gamma rho^c D mu^c
  *     + theta D rho^c ("log") -- the sign that makes grad mu = 0 the steady
  *     state (Eq. forceMuNid read as the force on the left of the momentum
@@ -40,15 +40,26 @@
  *
  * Data layout: f[c][i][y][x], rho[c][y][x], mom[c][d][y][x] (d = 0: x, 1: y).
  *
+ * Threads: when compiled with OpenMP, the rows of each stage are shared among
+ * threads.  Every node is still computed by the same arithmetic in the same
+ * order (no reduction crosses nodes, except the free energy, which stays serial),
+ * so the results are bitwise the same for any number of threads.
+ *
  * Parity status: every function is pinned by the oracle tests (closed forms,
  * invariants, the paper's explicit D1Q3 update, textbook coexistence, the
- * Maxwell-Stefan interdiffusion rate of Sec. IV for the friction lambda), except
- * lambda's role in nonlinear dynamics (coarsening, interface motion), which is
- * "parity unpinned".
+ * Maxwell-Stefan interdiffusion rate of Sec. IV for the friction lambda).  The
+ * "nid" force is pinned by its exact zero for an ideal mixture at gamma kT = theta
+ * and by its second-order agreement with the "log" force under refinement; the
+ * pivoted N-component friction solve by the closed-form uniform relaxation
+ * u_{n+1} = (D + L/2)^-1 (D - L/2) u_n.  Lambda's role in nonlinear dynamics
+ * (coarsening, interface motion) beyond these is "parity unpinned".
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_E_INVALID 1
@@ -137,6 +148,7 @@ int orc_moments(const orc_params *p, const double *f, double *rho, double *mom) 
     if (check_params(p, &L) != ORC_OK) return ORC_E_INVALID;
     long n = (long)p->nx * p->ny;
     for (int c = 0; c < p->ncomp; ++c)
+#pragma omp parallel for schedule(static)
         for (long s = 0; s < n; ++s) {
             double r = 0.0, jx = 0.0, jy = 0.0;
             for (int i = 0; i < L.q; ++i) {
@@ -164,6 +176,8 @@ int orc_mu(const orc_params *p, const double *rho, double *mu) {
     if (check_params(p, &L) != ORC_OK) return ORC_E_INVALID;
     long n = (long)p->nx * p->ny;
     int N = p->ncomp;
+    int bad = 0;
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < p->ny; ++y)
         for (int x = 0; x < p->nx; ++x) {
             long s = (long)y * p->nx + x;
@@ -172,10 +186,18 @@ int orc_mu(const orc_params *p, const double *rho, double *mu) {
                 eta -= p->b[c] * rho[(long)c * n + s];
                 rtot += rho[(long)c * n + s];
             }
-            if (!(eta > 0.0)) return ORC_E_DOMAIN;
+            if (!(eta > 0.0)) {
+#pragma omp atomic write
+                bad = 1;
+                continue;
+            }
             for (int c = 0; c < N; ++c) {
                 double rc = rho[(long)c * n + s];
-                if (!(rc > 0.0)) return ORC_E_DOMAIN;
+                if (!(rc > 0.0)) {
+#pragma omp atomic write
+                    bad = 1;
+                    continue;
+                }
                 double m = p->kT * log(rc / eta) + p->kT * p->b[c] * rtot / eta;
                 double inter = 0.0;
                 for (int cc = 0; cc < N; ++cc)
@@ -185,7 +207,7 @@ int orc_mu(const orc_params *p, const double *rho, double *mu) {
                 mu[(long)c * n + s] = m + 2.0 * inter;
             }
         }
-    return ORC_OK;
+    return bad ? ORC_E_DOMAIN : ORC_OK;
 }
 
 /* ---- lattice difference operators --------------------------------------- */
@@ -262,8 +284,11 @@ static int forces(const orc_params *p, const lattice_t *L, const double *rho, co
                   const double *mu, double *lnrho, double *G, double *Gmu) {
     long n = (long)p->nx * p->ny;
     int N = p->ncomp;
+    int bad = 0;
     if (p->force_method == 1)
+#pragma omp parallel for schedule(static)
         for (long s = 0; s < (long)N * n; ++s) lnrho[s] = log(rho[s]);
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < p->ny; ++y)
         for (int x = 0; x < p->nx; ++x) {
             long s = (long)y * p->nx + x;
@@ -304,14 +329,18 @@ static int forces(const orc_params *p, const lattice_t *L, const double *rho, co
                         rhs[c] -= W * (u0[c] - u0[cc]);
                     }
                 }
-                if (solve(N, A, rhs, gf) != ORC_OK) return ORC_E_DOMAIN;
+                if (solve(N, A, rhs, gf) != ORC_OK) {
+#pragma omp atomic write
+                    bad = 1;
+                    continue;
+                }
                 for (int c = 0; c < N; ++c) {
                     G[((long)c * L->d + a) * n + s] = gm[c][a] + gf[c];
                     if (Gmu) Gmu[((long)c * L->d + a) * n + s] = gm[c][a];
                 }
             }
         }
-    return ORC_OK;
+    return bad ? ORC_E_DOMAIN : ORC_OK;
 }
 
 /* ---- one timestep ---------------------------------------------------------- */
@@ -330,6 +359,7 @@ static int step(const orc_params *p, const lattice_t *L, double *f, work_t *w) {
     rc = forces(p, L, w->rho, w->mom, w->mu, w->lnrho, w->G, 0); /* stages 3, 4 */
     if (rc) return rc;
     for (int c = 0; c < N; ++c)
+#pragma omp parallel for schedule(static)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
                 long s = (long)y * p->nx + x;
@@ -447,6 +477,7 @@ int orc_equilibrium(const orc_params *p, const double *rho, const double *mom, d
     if (check_params(p, &L) != ORC_OK) return ORC_E_INVALID;
     long n = (long)p->nx * p->ny;
     for (int c = 0; c < p->ncomp; ++c)
+#pragma omp parallel for schedule(static)
         for (long s = 0; s < n; ++s) {
             double r = rho[(long)c * n + s];
             double u[2] = {0.0, 0.0};
@@ -496,3 +527,15 @@ int orc_free_energy(const orc_params *p, const double *rho, double *F, double *m
 }
 
 int orc_abi_q(int lattice) { return lattice == 1 ? 3 : (lattice == 2 ? 9 : 0); }
+
+/* Number of threads the stages use (1 without OpenMP); n < 1 leaves it unchanged.
+ * Returns the number in effect. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}

@@ -94,7 +94,8 @@ lb_status lb_rollout_forward(lb_ctx *c, int64_t nsteps, int32_t ckpt_every) {
     if (c->poisoned || !c->has_state) return rfail(c, LB_E_STATE, "fields not initialised or context poisoned");
     if (c->p.precision != LB_FP64 || c->p.force_method != LB_FORCE_LOG)
         return rfail(c, LB_E_INVALID, "the adjoint rollout needs an FP64 context with the log force");
-    if (cudaSetDevice(c->p.device) != cudaSuccess) return rfail(c, LB_E_CUDA, "cudaSetDevice");
+    DeviceGuard dg(c->p.device);
+    if (!dg.ok()) return rfail(c, LB_E_CUDA, "cudaSetDevice");
     for (double *p : c->ckpt) cudaFree(p);
     c->ckpt.clear();
     c->rollout_steps = -1;
@@ -127,7 +128,8 @@ lb_status lb_rollout_forward(lb_ctx *c, int64_t nsteps, int32_t ckpt_every) {
 lb_status lb_rollout_backward(lb_ctx *c, const double *rho_bar_T, double *rho_bar_0, double *grad) {
     if (!c || !rho_bar_T) return LB_E_INVALID;
     if (c->rollout_steps < 1) return rfail(c, LB_E_STATE, "no recorded rollout");
-    if (cudaSetDevice(c->p.device) != cudaSuccess) return rfail(c, LB_E_CUDA, "cudaSetDevice");
+    DeviceGuard dg(c->p.device);
+    if (!dg.ok()) return rfail(c, LB_E_CUDA, "cudaSetDevice");
     const int N = c->p.ncomp, Q = c->Q, D = c->D;
     const size_t n = c->n, state = (size_t)N * Q * n;
     const int k = c->ckpt_every;

@@ -8,6 +8,7 @@
 #include <string>
 
 #include "lbvdw.h"
+#include "lb_device_guard.cuh"
 #include "lb_launch.cuh"
 
 using namespace lbvdw;
@@ -114,8 +115,6 @@ lb_status usable(lb_ctx *c) {
     if (!c) return LB_E_INVALID;
     if (c->poisoned) return fail(c, LB_E_STATE, "context poisoned by an earlier error; set the fields again");
     if (!c->has_state) return fail(c, LB_E_STATE, "fields not initialised");
-    cudaError_t e = cudaSetDevice(c->p.device);
-    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
     return LB_OK;
 }
 
@@ -334,8 +333,8 @@ lb_status lb_create(const lb_params *p, lb_ctx **out) {
     c->elem = p->precision == LB_FP64 ? sizeof(double) : sizeof(float);
     c->stream = static_cast<cudaStream_t>(p->stream);
 
-    cudaError_t e = cudaSetDevice(p->device);
-    if (e != cudaSuccess) { delete c; return LB_E_CUDA; }
+    DeviceGuard dg(p->device);
+    if (!dg.ok()) { delete c; return LB_E_CUDA; }
     size_t fbytes = c->elem * (size_t)N * c->Q * c->n;
     size_t nparts = (c->n + DIAG_THREADS - 1) / DIAG_THREADS;
     if (nparts > 152 * 8) nparts = 152 * 8;
@@ -418,7 +417,8 @@ static lb_status device_mean(lb_ctx *c, const double *rho_dev, double *mean) {
 lb_status lb_init_fields(lb_ctx *c, const double *rho, const double *mom) {
     if (!c || !rho) return LB_E_INVALID;
     const int N = c->p.ncomp;
-    LB_CUDA(c, cudaSetDevice(c->p.device));
+    DeviceGuard dg(c->p.device);
+    LB_CUDA(c, dg.status);
     // the fields go to the device first; the reference densities and the domain check
     // (in the init kernel) are computed there
     LB_CUDA(c, cudaMemcpyAsync(c->rho, rho, sizeof(double) * N * c->n, cudaMemcpyHostToDevice, c->stream));
@@ -441,7 +441,8 @@ lb_status lb_init_fields(lb_ctx *c, const double *rho, const double *mom) {
 
 lb_status lb_init_fields_dev(lb_ctx *c, const double *rho_dev, const double *mom_dev) {
     if (!c || !rho_dev) return LB_E_INVALID;
-    LB_CUDA(c, cudaSetDevice(c->p.device));
+    DeviceGuard dg(c->p.device);
+    LB_CUDA(c, dg.status);
     double mean[4] = {0, 0, 0, 0};
     lb_status s = device_mean(c, rho_dev, mean);
     if (s != LB_OK) return s;
@@ -451,6 +452,8 @@ lb_status lb_init_fields_dev(lb_ctx *c, const double *rho_dev, const double *mom
 lb_status lb_step(lb_ctx *c, int64_t nsteps) {
     lb_status s = usable(c);
     if (s != LB_OK) return s;
+    DeviceGuard dg(c->p.device);
+    LB_CUDA(c, dg.status);
     if (nsteps < 0) return fail(c, LB_E_INVALID, "nsteps < 0");
     for (int64_t t = 0; t < nsteps; ++t) {
         cudaError_t e = run_step(c);
@@ -469,6 +472,8 @@ lb_status lb_step(lb_ctx *c, int64_t nsteps) {
 lb_status lb_read_moments_dev(lb_ctx *c, double *rho_dev, double *mom_dev) {
     lb_status s = usable(c);
     if (s != LB_OK) return s;
+    DeviceGuard dg(c->p.device);
+    LB_CUDA(c, dg.status);
     if (!rho_dev) return fail(c, LB_E_INVALID, "rho output is NULL");
     FieldLaunch a = field_args(c);
     a.rho_out = rho_dev;
@@ -482,6 +487,8 @@ lb_status lb_read_moments_dev(lb_ctx *c, double *rho_dev, double *mom_dev) {
 lb_status lb_read_moments(lb_ctx *c, double *rho, double *mom) {
     lb_status s = usable(c);
     if (s != LB_OK) return s;
+    DeviceGuard dg(c->p.device);
+    LB_CUDA(c, dg.status);
     if (!rho) return fail(c, LB_E_INVALID, "rho output is NULL");
     const int N = c->p.ncomp;
     FieldLaunch a = field_args(c);
@@ -497,6 +504,8 @@ lb_status lb_read_moments(lb_ctx *c, double *rho, double *mom) {
 lb_status lb_free_energy(lb_ctx *c, double *F, double *mass, double *mom_total) {
     lb_status s = usable(c);
     if (s != LB_OK) return s;
+    DeviceGuard dg(c->p.device);
+    LB_CUDA(c, dg.status);
     if (!F) return fail(c, LB_E_INVALID, "F output is NULL");
     const int N = c->p.ncomp;
     FieldLaunch a = field_args(c);
@@ -527,6 +536,8 @@ size_t lb_state_bytes(const lb_ctx *c) {
 lb_status lb_save_state(lb_ctx *c, void *buf, size_t bytes) {
     lb_status s = usable(c);
     if (s != LB_OK) return s;
+    DeviceGuard dg(c->p.device);
+    LB_CUDA(c, dg.status);
     if (!buf || bytes < lb_state_bytes(c)) return fail(c, LB_E_INVALID, "state buffer too small");
     StateHeader h;
     std::memset(&h, 0, sizeof h);
@@ -552,7 +563,8 @@ lb_status lb_load_state(lb_ctx *c, const void *buf, size_t bytes) {
         h.nx != c->p.nx || h.ny != c->p.ny || h.ncomp != c->p.ncomp || h.precision != c->p.precision ||
         h.hash != params_hash(c->p))
         return fail(c, LB_E_INVALID, "saved state does not match this context");
-    LB_CUDA(c, cudaSetDevice(c->p.device));
+    DeviceGuard dg(c->p.device);
+    LB_CUDA(c, dg.status);
     if (c->p.precision != LB_FP64) {
         double sum = 0.0;
         for (int k = 0; k < 4; ++k) sum += c->dp.rho_ref[k] * (k + 1);
@@ -583,7 +595,7 @@ lb_status lb_get_params(const lb_ctx *c, lb_params *out) {
 
 lb_status lb_destroy(lb_ctx *c) {
     if (!c) return LB_OK;
-    cudaSetDevice(c->p.device);
+    DeviceGuard dg(c->p.device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     cudaFree(c->f[0]);

@@ -252,7 +252,8 @@ lb_status lb_batch_create(const lb_params *shared, const lb_run_desc *runs, int3
             return LB_E_INVALID;  // the longest D1Q3 run does not fit one CTA's shared memory
         }
     }
-    if (cudaSetDevice(shared->device) != cudaSuccess) {
+    DeviceGuard dg(shared->device);
+    if (!dg.ok()) {
         delete b;
         return LB_E_CUDA;
     }
@@ -303,7 +304,8 @@ lb_status lb_batch_create(const lb_params *shared, const lb_run_desc *runs, int3
 lb_status lb_batch_init(lb_batch *b, const double *rho_all) {
     if (!b || !rho_all) return LB_E_INVALID;
     const int N = b->N;
-    LB_BCUDA(b, cudaSetDevice(b->shared.device));
+    DeviceGuard dg(b->shared.device);
+    LB_BCUDA(b, dg.status);
     size_t pos = 0;
     for (int r = 0; r < b->nruns; ++r) {
         const lb_run_desc &d = b->desc[r];
@@ -364,7 +366,8 @@ lb_status lb_batch_step(lb_batch *b, int64_t nsteps) {
     if (!b) return LB_E_INVALID;
     if (!b->has_state) return bfail(b, LB_E_STATE, "fields not initialised");
     if (nsteps < 0) return bfail(b, LB_E_INVALID, "nsteps < 0");
-    LB_BCUDA(b, cudaSetDevice(b->shared.device));
+    DeviceGuard dg(b->shared.device);
+    LB_BCUDA(b, dg.status);
     int64_t left = nsteps;
     while (left > 0) {
         int len = left >= GRAPH_CHUNK ? GRAPH_CHUNK : (int)left;
@@ -383,7 +386,8 @@ lb_status lb_batch_step(lb_batch *b, int64_t nsteps) {
 lb_status lb_batch_read(lb_batch *b, int32_t run, double *rho, double *mom) {
     if (!b || !rho || run < 0 || run >= b->nruns) return LB_E_INVALID;
     if (!b->has_state) return bfail(b, LB_E_STATE, "fields not initialised");
-    LB_BCUDA(b, cudaSetDevice(b->shared.device));
+    DeviceGuard dg(b->shared.device);
+    LB_BCUDA(b, dg.status);
     const lb_run_desc &d = b->desc[run];
     const size_t n = (size_t)d.nx * d.ny;
     const int D = d.lattice == LB_D1Q3 ? 1 : 2;
@@ -409,7 +413,8 @@ lb_status lb_batch_read(lb_batch *b, int32_t run, double *rho, double *mom) {
 
 lb_status lb_batch_errors(lb_batch *b, uint32_t *flags) {
     if (!b || !flags) return LB_E_INVALID;
-    LB_BCUDA(b, cudaSetDevice(b->shared.device));
+    DeviceGuard dg(b->shared.device);
+    LB_BCUDA(b, dg.status);
     LB_BCUDA(b, cudaMemcpyAsync(flags, b->d_err, sizeof(unsigned) * b->nruns, cudaMemcpyDeviceToHost, b->stream));
     LB_BCUDA(b, cudaStreamSynchronize(b->stream));
     return LB_OK;
@@ -420,7 +425,8 @@ lb_status lb_batch_set_tile(lb_batch *b, int32_t tile_x, int32_t tile_y) {
     bool ok = (tile_x == 32 && tile_y == 8) || (tile_x == 64 && tile_y == 4) || (tile_x == 32 && tile_y == 16) ||
               (tile_x == 64 && tile_y == 8);
     if (!ok) return bfail(b, LB_E_INVALID, "unsupported tile");
-    LB_BCUDA(b, cudaSetDevice(b->shared.device));
+    DeviceGuard dg(b->shared.device);
+    LB_BCUDA(b, dg.status);
     LB_BCUDA(b, cudaStreamSynchronize(b->stream));
     clear_graphs(b);
     b->tile_x = tile_x;
@@ -432,7 +438,8 @@ lb_status lb_batch_set_tile(lb_batch *b, int32_t tile_x, int32_t tile_y) {
 
 lb_status lb_batch_time_steps(lb_batch *b, int32_t nsteps, double *ms) {
     if (!b || !ms || nsteps < 1) return LB_E_INVALID;
-    LB_BCUDA(b, cudaSetDevice(b->shared.device));
+    DeviceGuard dg(b->shared.device);
+    LB_BCUDA(b, dg.status);
     cudaEvent_t e0, e1;
     LB_BCUDA(b, cudaEventCreate(&e0));
     LB_BCUDA(b, cudaEventCreate(&e1));
@@ -456,7 +463,7 @@ const char *lb_batch_last_error(const lb_batch *b) { return b ? b->msg.c_str() :
 
 lb_status lb_batch_destroy(lb_batch *b) {
     if (!b) return LB_OK;
-    cudaSetDevice(b->shared.device);
+    DeviceGuard dg(b->shared.device);
     if (b->stream) cudaStreamSynchronize(b->stream);
     else cudaDeviceSynchronize();
     clear_graphs(b);

@@ -2,6 +2,7 @@
 // Each lattice/precision pair lives in its own .cu file so the library builds in
 // parallel; lb_api.cu dispatches to them.
 #pragma once
+#include "lb_device_guard.cuh"
 #include "lb_kernels.cuh"
 #include "lbvdw.h"
 

@@ -15,11 +15,13 @@
 // shared by every call on a device and keeps the last call's contents; the error word is
 // cleared at the start of each call.  Calls that overlap on the GPU (on different
 // streams, or from different host threads) race on it: serialise them.  In host code the
-// symbol is only a host-side stand-in, so the device address is obtained once per device
-// with cudaGetSymbolAddress (that device current) during the first call on the device;
-// make that first call before any stream capture.
-#include <mutex>
-
+// symbol is only a host-side stand-in, so every call looks up the array's device address
+// with cudaGetSymbolAddress (the call's device current; the lookup allocates nothing).
+// Looking it up on every call, rather than caching it, keeps the address right after a
+// device reset or a new primary context.  The first call on a device also loads the
+// library's module there, so make it before any stream capture.  The caller's current
+// device is restored before the call returns.
+#include "lb_device_guard.cuh"
 #include "lb_kernels.cuh"
 #include "lbvdw.h"
 
@@ -36,21 +38,12 @@ constexpr size_t NOALLOC_FIELD_DOUBLES = NOALLOC_SCRATCH_DOUBLES - NOALLOC_PARTI
 
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
 
-constexpr int MAX_DEVICES = 64;
-std::mutex g_mutex;
-double *g_scratch_addr[MAX_DEVICES] = {nullptr};
-
-// device address of the scratch array on the current device (resolved once per device)
-cudaError_t scratch_address(int device, double **out) {
-    if (device < 0 || device >= MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[device] = static_cast<double *>(p);
-    }
-    *out = g_scratch_addr[device];
+// device address of the scratch array on the current device
+cudaError_t scratch_address(double **out) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<double *>(p);
     return cudaSuccess;
 }
 
@@ -108,9 +101,10 @@ extern "C" lb_status lb_free_energy_noalloc(const lb_params *p, const void *f_de
         if (!(p->b[c] > 0.0)) return LB_E_INVALID;
         if (p->precision != LB_FP64 && !(p->rho_ref[c] > 0.0)) return LB_E_INVALID;
     }
-    if (cudaSetDevice(p->device) != cudaSuccess) return LB_E_CUDA;
+    DeviceGuard dg(p->device);
+    if (!dg.ok()) return LB_E_CUDA;
     double *scratch = nullptr;
-    if (scratch_address(p->device, &scratch) != cudaSuccess) return LB_E_CUDA;
+    if (scratch_address(&scratch) != cudaSuccess) return LB_E_CUDA;
 
     DevParams P{};
     P.nx = p->nx;

@@ -2,6 +2,7 @@
 // (include/lbvdw_selftest.h).
 #include <cstring>
 
+#include "lb_device_guard.cuh"
 #include "lb_kernels.cuh"
 #include "lb_strip.cuh"
 #include "lbvdw_selftest.h"
@@ -51,7 +52,8 @@ __global__ void selftest_wait_kernel(unsigned *flag, unsigned polls, int arrive)
 
 extern "C" lb_status lb_selftest_wait(int32_t device, uint32_t polls, int32_t arrive, uint32_t *flag) {
     if (!flag || polls < 1) return LB_E_INVALID;
-    if (cudaSetDevice(device) != cudaSuccess) return LB_E_CUDA;
+    lbvdw::DeviceGuard dg(device);
+    if (!dg.ok()) return LB_E_CUDA;
     unsigned *d = nullptr;
     if (cudaMalloc(&d, sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
@@ -73,7 +75,8 @@ extern "C" lb_status lb_selftest_wait(int32_t device, uint32_t polls, int32_t ar
 extern "C" lb_status lb_selftest_log(int32_t device, const double *x, int64_t n, double *out_tbl, double *out_df,
                                      double *out_ref) {
     if (!x || !out_tbl || !out_df || !out_ref || n < 1) return LB_E_INVALID;
-    if (cudaSetDevice(device) != cudaSuccess) return LB_E_CUDA;
+    lbvdw::DeviceGuard dg(device);
+    if (!dg.ok()) return LB_E_CUDA;
     lbvdw::LogTables h;
     lbvdw::fill_log_tables(&h);
     double *d = nullptr;
@@ -104,7 +107,8 @@ extern "C" lb_status lb_selftest_log(int32_t device, const double *x, int64_t n,
 
 extern "C" lb_status lb_selftest_recip(int32_t device, const double *x, int64_t n, double *out_df) {
     if (!x || !out_df || n < 1) return LB_E_INVALID;
-    if (cudaSetDevice(device) != cudaSuccess) return LB_E_CUDA;
+    lbvdw::DeviceGuard dg(device);
+    if (!dg.ok()) return LB_E_CUDA;
     double *d = nullptr;
     size_t bytes = sizeof(double) * (size_t)n;
     if (cudaMalloc(&d, 2 * bytes) != cudaSuccess) {

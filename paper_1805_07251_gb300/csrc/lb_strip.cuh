@@ -259,8 +259,10 @@ __global__ void __launch_bounds__(StripLayout<N, TX, TY, MU>::NT, 2)
     unsigned bad = 0;
 
     // prologue: rho on rows [ys-2, ys+2) (the last 4 rows of block 0), mu on [ys-1, ys+1)
-    if (!mbar_wait_bounded(bar + 0, 0)) atomicOr(&s_abort, 1u);
-    waited = 1;
+    // `waited` advances only past blocks whose wait succeeded, so that an abort drains
+    // the block that timed out as well as every later one
+    if (mbar_wait_bounded(bar + 0, 0)) waited = 1;
+    else atomicOr(&s_abort, 1u);
     strip_rho<N, TX, TY, R, MU>(pop, s_rho, P, 0, TY - 4, 4, tid);
     __syncthreads();
     if (!strip_mu<N, TX, TY, R, FORCE, MU>(s_rho, s_phi, s_tbl, P, 1, 2, tid)) bad = 1;
@@ -274,8 +276,8 @@ __global__ void __launch_bounds__(StripLayout<N, TX, TY, MU>::NT, 2)
             strip_issue<N, TX, TY, MU>(fin, pop, bar, k + 2, ys, x0, nx, ny, plane, tid);
             issued = k + 3;
         }
-        if (!mbar_wait_bounded(bar + (k + 1) % 3, ((k + 1) / 3) & 1)) atomicOr(&s_abort, 1u);
-        waited = k + 2;
+        if (mbar_wait_bounded(bar + (k + 1) % 3, ((k + 1) / 3) & 1)) waited = k + 2;
+        else atomicOr(&s_abort, 1u);
         // rho on the rows of block k+1: [y+2, y+TY+2)
         strip_rho<N, TX, TY, R, MU>(pop, s_rho, P, k + 1, 0, TY, tid);
         __syncthreads();

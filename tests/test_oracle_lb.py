@@ -79,6 +79,106 @@ def test_friction_relaxation_closed_form(lattice, ny, direction, lam):
         assert np.max(np.abs(j.sum(axis=(0, 2, 3)) - P0)) < 1e-15
 
 
+# symmetric friction matrix with distinct pair values and unequal densities, so that a
+# transposed or shifted index, or a wrong sign, changes the result
+LAM4 = np.array([[0.0, 0.5, 2.0, 1.3], [0.5, 0.0, 0.8, 3.0], [2.0, 0.8, 0.0, 0.25], [1.3, 3.0, 0.25, 0.0]])
+RHO4 = np.array([0.3, 0.55, 0.42, 0.2])
+
+
+@pytest.mark.parametrize("lattice,ny", [("D1Q3", 1), ("D2Q9", 4)])
+@pytest.mark.parametrize("N", [3, 4])
+def test_friction_n_components_uniform_relaxation_closed_form(lattice, ny, N):
+    # Eq. forceFriction for N components: on a uniform state the mean-field force
+    # vanishes, and the friction gain G = -L u-hat with u-hat = u + D^-1 G / 2 (D = diag
+    # rho, L the weighted Laplacian of W^{cc'} = lambda^{cc'} rho^c rho^c' / (rho^c +
+    # rho^c')) is the step's whole momentum change, j_{n+1} = j_n + G_n.  Eliminating G:
+    #   u_{n+1} = (D + L/2)^-1 (D - L/2) u_n,
+    # built here from the equation with numpy, independently of the oracle's pivoted
+    # per-node solve.  1^T L = 0 makes the total momentum sum_c rho^c u^c invariant.
+    L = lat(lattice, 6, ny, N, lam=LAM4[:N, :N], b=np.full(N, 0.3))
+    d = L.d
+    u0 = np.random.default_rng(7).normal(0.0, 0.01, (N, d))
+    rho = np.empty(L.rshape())
+    mom = np.zeros(L.mshape())
+    for c in range(N):
+        rho[c] = RHO4[c]
+        for a in range(d):
+            mom[c, a] = RHO4[c] * u0[c, a]
+    W = np.zeros((N, N))
+    for c in range(N):
+        for cc in range(N):
+            if c != cc:
+                W[c, cc] = LAM4[c, cc] * RHO4[c] * RHO4[cc] / (RHO4[c] + RHO4[cc])
+    Lap = np.diag(W.sum(axis=1)) - W
+    D = np.diag(RHO4[:N])
+    M = np.linalg.solve(D + 0.5 * Lap, D - 0.5 * Lap)
+    P0 = (RHO4[:N, None] * u0).sum(axis=0)
+    f = L.equilibrium(rho, mom)
+    u = u0.copy()
+    for n in range(1, 6):
+        f = L.run(f, 1)
+        u = M @ u
+        r, j = L.moments(f)
+        ug = (j / r[:, None]).reshape(N, d, -1)
+        # u of order 1e-2: 1e-15 absolute is the rounding of the populations' moments
+        assert np.max(np.abs(ug - u[:, :, None])) < 1e-15
+        assert np.max(np.abs(r - rho)) < 1e-15
+        P = j.sum(axis=(0, 2, 3)) / L.nodes
+        assert np.max(np.abs(P - P0)) < 1e-16
+    # the relaxation is real: the velocities moved by far more than the tolerance
+    assert np.max(np.abs(u - u0)) > 1e-3
+
+
+def test_nid_force_vanishes_for_ideal_mixture_at_matching_temperature():
+    # Eq. forceMuId: G^{mu,c} = -rho^c D(gamma mu^c - theta ln rho^c).  With no attraction
+    # (a = kappa = 0) and no excluded volume (b = 0), Eq. discreteChemicalPotential gives
+    # mu^c = kT ln rho^c, so for gamma kT = theta the bracket vanishes identically and the
+    # force is zero to rounding on any profile, while the "log" form (Eq. forceMuLog), a
+    # different discretisation, leaves a residual of the order of the gradients.
+    for lattice, nx, ny in (("D1Q3", 64, 1), ("D2Q9", 24, 20)):
+        for kT in (THETA, 0.7):
+            kw = dict(kT=kT, gamma=THETA / kT, a=np.zeros((2, 2)), kappa=0.0, b=[0.0, 0.0], lam=1.0)
+            Lnid = lat(lattice, nx, ny, 2, force_method=1, **kw)
+            Llog = lat(lattice, nx, ny, 2, force_method=0, **kw)
+            rho = noisy(Lnid, [0.4, 0.7], 0.05, 3)
+            f = Lnid.equilibrium(rho)
+            G, Gmu = Lnid.forces(f)
+            assert np.max(np.abs(Gmu)) < 1e-16
+            assert np.max(np.abs(G)) < 1e-16       # at rest: no friction either
+            _, Gmu_log = Llog.forces(f)
+            assert np.max(np.abs(Gmu_log)) > 1e-3
+
+
+@pytest.mark.parametrize("lattice", ["D1Q3", "D2Q9"])
+def test_nid_and_log_forces_converge_at_second_order(lattice):
+    # Both forces discretise the same continuum force, -gamma rho grad mu + theta grad rho
+    # (rho grad ln rho = grad rho): they differ by theta (rho D ln rho - D rho), which for
+    # second-order central differences is O(k^3) on a wave of wavenumber k, against a
+    # force of O(k).  Refining the lattice (same profile on 2x the nodes) must divide the
+    # difference by 8 and the relative difference by 4.
+    a = np.array([[1.0, 0.9], [0.9, 0.6]])
+    diffs, forces = [], []
+    for n in (32, 64, 128, 256):
+        ny = 1 if lattice == "D1Q3" else n
+        kw = dict(kT=0.73, gamma=0.35, a=a, b=[0.25, 0.3], kappa=0.1)
+        Lnid = lat(lattice, n, ny, 2, force_method=1, **kw)
+        Llog = lat(lattice, n, ny, 2, force_method=0, **kw)
+        x = np.arange(n)[None, :]
+        y = np.arange(ny)[:, None]
+        ph = 2 * np.pi * (x + (y if lattice == "D2Q9" else 0)) / n     # diagonal wave in 2-D
+        rho = np.stack([0.48 + 0.1 * np.sin(ph), 0.72 + 0.08 * np.cos(ph + 0.3)])
+        f = Lnid.equilibrium(rho)
+        _, g_nid = Lnid.forces(f)
+        _, g_log = Llog.forces(f)
+        diffs.append(np.max(np.abs(g_nid - g_log)))
+        forces.append(np.max(np.abs(g_log)))
+    diffs, forces = np.array(diffs), np.array(forces)
+    order_abs = np.log2(diffs[:-1] / diffs[1:])
+    order_rel = np.log2((diffs / forces)[:-1] / (diffs / forces)[1:])
+    assert np.all(np.abs(order_abs[1:] - 3.0) < 0.05) and abs(order_abs[0] - 3.0) < 0.1
+    assert np.all(np.abs(order_rel[1:] - 2.0) < 0.05) and abs(order_rel[0] - 2.0) < 0.1
+
+
 def test_momentum_bookkeeping():
     # Sec. III: collision and friction conserve the total momentum; the only change is
     # the sum over nodes of the mean-field forces (whose ideal part telescopes).
