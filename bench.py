@@ -408,12 +408,45 @@ def richardson(fun, x0, h):
     return (16 * r2 - r1) / 15, d[0]
 
 
+class MemPeak:
+    """Lowest free device memory seen while a call runs (polled from a host thread every
+    5 ms through cudaMemGetInfo): the call's peak device memory is the drop from before."""
+
+    def __init__(self, torch, dev):
+        import threading
+
+        self.torch, self.dev = torch, dev
+        self.free0 = torch.cuda.mem_get_info(dev)[0]
+        self.low = self.free0
+        self.stop_ev = threading.Event()
+        self.th = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        while not self.stop_ev.is_set():
+            self.low = min(self.low, self.torch.cuda.mem_get_info(self.dev)[0])
+            time.sleep(0.005)
+
+    def __enter__(self):
+        self.th.start()
+        return self
+
+    def __exit__(self, *exc):
+        self.stop_ev.set()
+        self.th.join()
+
+    @property
+    def peak_bytes(self):
+        return self.free0 - self.low
+
+
 def time_adjoint(torch, dev):
     """Workload c5: D2Q9, 2 components, 512^2, config-2 mixture and temperature with
-    a12 = 0.75, 2000 FP64 steps checkpointed every 100; loss = sum (rho_T - rho_target)^2
-    with the target from the FP64 forward at a12 = 0.8.  Times one gradient (forward with
-    checkpoints + backward) and checks it against central finite differences (h = 1e-4,
-    Richardson-extrapolated)."""
+    a12 = 0.75, 2000 steps checkpointed every 100; loss = sum (rho_T - rho_target)^2 with
+    the target from the FP64 forward at a12 = 0.8.  Times one gradient (forward with
+    checkpoints + backward) of the FP64 rollout and of the two FP32-storage rollouts (FP32
+    adjoint, FP64 mu), and checks each against central finite differences of the FP64
+    forward (h = 1e-4: plain and Richardson-extrapolated) and the FP32 ones against the
+    FP64 adjoint.  Peak device memory of each rollout (checkpoints + backward) is polled."""
     import numpy as np
 
     import lbinputs
@@ -424,11 +457,12 @@ def time_adjoint(torch, dev):
     rho0 = lbinputs.fields("c5")
     st = torch.cuda.current_stream(dev).cuda_stream
 
-    def make(a12, kap):
+    def make(a12, kap, precision="fp64"):
         a = p["a"].copy()
         a[0, 1] = a[1, 0] = a12
         return Simulation(lattice="D2Q9", nx=n, ny=n, ncomp=2, tau=1.0, kT=p["kT"], gamma_mu=p["gamma_mu"], a=a,
-                          kappa=np.full((2, 2), kap), lam=p["lam"], b=p["b"], precision="fp64", device=dev, stream=st)
+                          kappa=np.full((2, 2), kap), lam=p["lam"], b=p["b"], precision=precision, device=dev,
+                          stream=st)
 
     def final(a12, kap, r0):
         s = make(a12, kap)
@@ -443,30 +477,54 @@ def time_adjoint(torch, dev):
     def loss(a12, kap, r0=rho0):
         return float(np.sum((final(a12, kap, r0) - tgt) ** 2))
 
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    s = make(0.75, 0.1)
-    s.init(rho0)
-    capi.lb_rollout_forward(s.ctx, steps, ckpt)
-    r, _ = s.moments()
-    t1 = time.perf_counter()
-    rb0, g = capi.lb_rollout_backward(s.ctx, 2.0 * (r - tgt), 2)
-    t2 = time.perf_counter()
-    s.close()
-    ga, gk = g[1] + g[2], g[4:8].sum()
-    fa, fa0 = richardson(lambda v: loss(v, 0.1), 0.75, 1e-4)
-    fk, fk0 = richardson(lambda v: loss(0.75, v), 0.1, 1e-4)
     v = 1e-2 * np.random.default_rng(5).normal(0, 1, rho0.shape)
+
+    def gradient(precision):
+        torch.cuda.synchronize(dev)
+        with MemPeak(torch, dev) as mp:
+            t0 = time.perf_counter()
+            s = make(0.75, 0.1, precision)
+            s.init(rho0)
+            capi.lb_rollout_forward(s.ctx, steps, ckpt)
+            r, _ = s.moments()
+            t1 = time.perf_counter()
+            rb0, g = capi.lb_rollout_backward(s.ctx, 2.0 * (r - tgt), 2)
+            t2 = time.perf_counter()
+            s.close()
+        return dict(ga=g[1] + g[2], gk=g[4:8].sum(), gr=float(np.sum(rb0 * v)), total=t2 - t0, fwd=t1 - t0,
+                    bwd=t2 - t1, mem=mp.peak_bytes)
+
+    g64 = gradient("fp64")
+    fa, fa0 = richardson(lambda x: loss(x, 0.1), 0.75, 1e-4)
+    fk, fk0 = richardson(lambda x: loss(0.75, x), 0.1, 1e-4)
     fr, fr0 = richardson(lambda t: loss(0.75, 0.1, rho0 + t * v), 0.0, 1e-4)
-    gr = float(np.sum(rb0 * v))
-    return {"workload": "D2Q9, 2 components, %dx%d, a12 = 0.75, gamma_mu = %.4g, %d FP64 steps, checkpoint every %d"
-                        % (n, n, p["gamma_mu"], steps, ckpt),
-            "s_per_gradient": t2 - t0, "forward_s": t1 - t0, "backward_s": t2 - t1,
-            "grad_a12": ga, "fd_a12": fa, "rel_err_a12": abs(ga - fa) / abs(fa),
-            "grad_kappa": gk, "fd_kappa": fk, "rel_err_kappa": abs(gk - fk) / abs(fk),
-            "grad_rho0_dir": gr, "fd_rho0_dir": fr, "rel_err_rho0_dir": abs(gr - fr) / abs(fr),
-            "fd_plain_h1e-4": {"a12": fa0, "kappa": fk0, "rho0_dir": fr0},
-            "dtype": "f64 (forward and adjoint)"}
+    out = {"workload": "D2Q9, 2 components, %dx%d, a12 = 0.75, gamma_mu = %.4g, %d steps, checkpoint every %d"
+                       % (n, n, p["gamma_mu"], steps, ckpt),
+           "s_per_gradient": g64["total"], "forward_s": g64["fwd"], "backward_s": g64["bwd"],
+           "peak_device_bytes": g64["mem"],
+           "grad_a12": g64["ga"], "fd_a12": fa, "rel_err_a12": abs(g64["ga"] - fa) / abs(fa),
+           "grad_kappa": g64["gk"], "fd_kappa": fk, "rel_err_kappa": abs(g64["gk"] - fk) / abs(fk),
+           "grad_rho0_dir": g64["gr"], "fd_rho0_dir": fr, "rel_err_rho0_dir": abs(g64["gr"] - fr) / abs(fr),
+           "fd_plain_h1e-4": {"a12": fa0, "kappa": fk0, "rho0_dir": fr0},
+           "rel_err_vs_plain_fd": {"a12": abs(g64["ga"] - fa0) / abs(fa0), "kappa": abs(g64["gk"] - fk0) / abs(fk0),
+                                   "rho0_dir": abs(g64["gr"] - fr0) / abs(fr0)},
+           "dtype": "f64 (forward and adjoint)"}
+    for precision, key in (("fp32_mixed", "fp32_fp64mu"), ("fp32_dfmu", "fp32_dfmu")):
+        g = gradient(precision)
+        out[key] = {
+            "dtype": "f32 storage and adjoint, %s mu in the forward, f64 mu in the adjoint"
+                     % ("f64" if precision == "fp32_mixed" else "double-float"),
+            "s_per_gradient": g["total"], "forward_s": g["fwd"], "backward_s": g["bwd"],
+            "peak_device_bytes": g["mem"],
+            "grad_a12": g["ga"], "grad_kappa": g["gk"], "grad_rho0_dir": g["gr"],
+            "rel_diff_vs_fp64_adjoint": {"a12": abs(g["ga"] - g64["ga"]) / abs(g64["ga"]),
+                                         "kappa": abs(g["gk"] - g64["gk"]) / abs(g64["gk"]),
+                                         "rho0_dir": abs(g["gr"] - g64["gr"]) / abs(g64["gr"])},
+            "rel_err_vs_fd_richardson": {"a12": abs(g["ga"] - fa) / abs(fa), "kappa": abs(g["gk"] - fk) / abs(fk),
+                                         "rho0_dir": abs(g["gr"] - fr) / abs(fr)},
+            "rel_err_vs_fd_plain_h1e-4": {"a12": abs(g["ga"] - fa0) / abs(fa0), "kappa": abs(g["gk"] - fk0) / abs(fk0),
+                                          "rho0_dir": abs(g["gr"] - fr0) / abs(fr0)}}
+    return out
 
 
 def time_path(torch, Simulation, kw, rho, precision, steps, warmup, flush, dev):

@@ -212,21 +212,27 @@ lb_status lb_free_energy_noalloc(const lb_params *p, const void *f_dev, double *
 /* ---- adjoint rollout -----------------------------------------------------------------
  * Reverse-mode gradients of a loss of the final densities with respect to the initial
  * densities and the mixture parameters a, kappa, b, through the hand-written transpose
- * of the fused timestep (FP64 contexts, "log" force).  Long rollouts keep a copy of the
- * state every ckpt_every steps and recompute each segment during the backward pass. */
+ * of the fused timestep (Eqs. LBequation, BGKcollisionOperator, feq, forceCorrectionsPsi,
+ * forceFriction, forceMuLog, discreteChemicalPotential; "log" force).  FP64 contexts get
+ * an FP64 adjoint; FP32-storage contexts (LB_FP32_MIXED, LB_FP32_DFMU) an FP32 adjoint
+ * whose chemical-potential recompute and Jacobian run in FP64, linearised at the FP32
+ * forward trajectory.  Long rollouts keep a copy of the state every ckpt_every steps and
+ * recompute each segment during the backward pass with the forward's own step kernel. */
 
-/* Advance nsteps >= 1 FP64 timesteps from the current state (which must come from
+/* Advance nsteps >= 1 timesteps from the current state (which must come from
  * lb_init_fields with mom = NULL for rho_bar_0 below to be the gradient with respect to
- * the initial densities), keeping (nsteps / ckpt_every + 1) device checkpoints.
- * Errors: LB_E_INVALID (not FP64 / not the log force), LB_E_STATE, LB_E_NOMEM, LB_E_CUDA. */
+ * the initial densities), keeping (nsteps / ckpt_every + 1) device checkpoints in the
+ * context's storage type.  Errors: LB_E_INVALID (precision LB_FP32 or the nid force),
+ * LB_E_STATE, LB_E_NOMEM, LB_E_CUDA. */
 lb_status lb_rollout_forward(lb_ctx *ctx, int64_t nsteps, int32_t ckpt_every);
 
 /* Given rho_bar_T = dL/d rho at the end of the recorded rollout (host [c][y][x]), return
  * rho_bar_0 = dL/d rho_0 (host [c][y][x], may be NULL) and grad (host, may be NULL) =
  * [dL/da_cd (ncomp x ncomp, each entry taken as independent), dL/dkappa_cd (ncomp x ncomp),
  * dL/db_c (ncomp)].  For a symmetric pair a_12 = a_21 the gradient of the shared value is
- * the sum of the two entries.  Allocates ckpt_every states plus work arrays (FP64) for the
- * duration of the call; synchronises.  Errors: LB_E_INVALID, LB_E_STATE (no rollout),
+ * the sum of the two entries.  Allocates ckpt_every states plus work arrays (in the
+ * storage type; moments, chemical potential and gradient sums in FP64) for the duration
+ * of the call; synchronises.  Errors: LB_E_INVALID, LB_E_STATE (no rollout),
  * LB_E_NOMEM, LB_E_CUDA. */
 lb_status lb_rollout_backward(lb_ctx *ctx, const double *rho_bar_T, double *rho_bar_0, double *grad);
 

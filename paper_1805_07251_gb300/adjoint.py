@@ -1,6 +1,7 @@
 """Differentiable rollouts: ``LBRollout`` is a ``torch.autograd.Function`` whose forward
-advances an FP64 run on the GPU (checkpointing every ``ckpt_every`` steps) and whose
-backward calls the library's hand-written adjoint of the fused timestep
+advances a run on the GPU (checkpointing every ``ckpt_every`` steps; ``spec["precision"]``
+"fp64" by default, or "fp32_mixed" / "fp32_dfmu" for FP32 storage with an FP32 adjoint)
+and whose backward calls the library's hand-written adjoint of the fused timestep
 (``lb_rollout_backward``).  Gradients flow to a_12 (the shared value of the symmetric
 pair a_12 = a_21), to kappa (one value for every pair, as in the workloads), to b and to
 the initial densities.  The torch tensors are plumbing: every step of the rollout and of
@@ -28,7 +29,7 @@ class LBRollout(torch.autograd.Function):
         r0 = rho0.detach().cpu().numpy().astype(np.float64)
         sim = Simulation(lattice=spec["lattice"], nx=r0.shape[2], ny=r0.shape[1], ncomp=N, tau=spec["tau"],
                          kT=spec["kT"], gamma_mu=spec["gamma_mu"], a=a, kappa=kap, lam=spec["lam"], b=bb,
-                         precision="fp64", device=spec.get("device", 0))
+                         precision=spec.get("precision", "fp64"), device=spec.get("device", 0))
         sim.init(r0)
         capi.lb_rollout_forward(sim.ctx, spec["steps"], spec.get("ckpt_every", 100))
         rho_T, _ = sim.moments()

@@ -1,5 +1,11 @@
-// lb_adjoint.cuh -- hand-written adjoint (vector-Jacobian product) of one FP64 timestep
-// of the fused step (lb_kernels.cuh), "log" force.
+// lb_adjoint.cuh -- hand-written adjoint (vector-Jacobian product) of one timestep of the
+// fused step (lb_kernels.cuh), "log" force.
+//
+// The kernels are templates over T, the type of the adjoint populations and of their
+// arithmetic: double for the FP64 rollout, float for the FP32 rollouts.  In both, the
+// forward recompute of the chemical potential (phi = gamma mu, its gradient) and the
+// transpose of its Jacobian d mu / d rho run in FP64, the moments of the forward state
+// arrive in FP64, and the parameter-gradient partials are summed in FP64.
 //
 // Forward step (per node x, component c; D = central difference, Lap = lattice
 // Laplacian, theta = 1/3):
@@ -27,10 +33,12 @@ namespace lbvdw {
 
 constexpr int ADJ_THREADS = 256;
 
+template <class T>
 struct AdjArrays {
-    const double *rho, *j;       // [N][n], [N][D][n] at step t
-    double *lap, *phi;           // [N][n]
-    double *rhob, *jb, *dphib, *drhob, *lapb, *mub;  // adjoint intermediates
+    const double *rho, *j;       // [N][n], [N][D][n] at step t (FP64 moments of the state)
+    T *lap;                      // [N][n]
+    double *phi;                 // [N][n], gamma mu in FP64
+    T *rhob, *jb, *dphib, *drhob, *lapb, *mub;  // adjoint intermediates
     double *partial;             // [blocks][2 N^2 + N] parameter-gradient partials
 };
 
@@ -45,34 +53,34 @@ struct Nb {
     }
 };
 
-// D_alpha phi = (1/theta) sum_i w_i v_i,alpha phi(x + v_i)
-template <int LAT>
-__device__ inline void grad_g(const double *phi, int x, int y, int nx, int ny, double &gx, double &gy) {
+// D_alpha phi = (1/theta) sum_i w_i v_i,alpha phi(x + v_i), in the arithmetic of the array
+template <int LAT, class A>
+__device__ inline void grad_g(const A *phi, int x, int y, int nx, int ny, A &gx, A &gy) {
     using L = Lat<LAT>;
-    double ax = 0.0, ay = 0.0;
+    A ax = A(0), ay = A(0);
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
-        double v = phi[Nb<LAT>::at(x, y, i, nx, ny)];
-        ax += L::w(i) * L::vx(i) * v;
-        ay += L::w(i) * L::vy(i) * v;
+        A v = phi[Nb<LAT>::at(x, y, i, nx, ny)];
+        ax += A(L::w(i) * L::vx(i)) * v;
+        ay += A(L::w(i) * L::vy(i)) * v;
     }
-    gx = 3.0 * ax;
-    gy = 3.0 * ay;
+    gx = A(3) * ax;
+    gy = A(3) * ay;
 }
 
-template <int LAT>
-__device__ inline double lap_g(const double *phi, int x, int y, int nx, int ny) {
+template <int LAT, class A>
+__device__ inline A lap_g(const A *phi, int x, int y, int nx, int ny) {
     using L = Lat<LAT>;
-    const double c = phi[(size_t)y * nx + x];
-    double acc = 0.0;
+    const A c = phi[(size_t)y * nx + x];
+    A acc = A(0);
 #pragma unroll
-    for (int i = 1; i < L::Q; ++i) acc += L::w(i) * (phi[Nb<LAT>::at(x, y, i, nx, ny)] - c);
-    return 6.0 * acc;
+    for (int i = 1; i < L::Q; ++i) acc += A(L::w(i)) * (phi[Nb<LAT>::at(x, y, i, nx, ny)] - c);
+    return A(6) * acc;
 }
 
-// ---- forward recompute: Lap rho and phi = gamma mu ------------------------------------
-template <int LAT, int N>
-__global__ void __launch_bounds__(ADJ_THREADS) adj_mu_kernel(AdjArrays A, DevParams P) {
+// ---- forward recompute: Lap rho and phi = gamma mu (FP64) -----------------------------
+template <int LAT, int N, class T>
+__global__ void __launch_bounds__(ADJ_THREADS) adj_mu_kernel(AdjArrays<T> A, DevParams P) {
     const size_t n = (size_t)P.nx * P.ny;
     const size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -82,7 +90,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_mu_kernel(AdjArrays A, DevPar
     for (int c = 0; c < N; ++c) {
         r[c] = A.rho[c * n + s];
         lp[c] = lap_g<LAT>(A.rho + c * n, x, y, P.nx, P.ny);
-        A.lap[c * n + s] = lp[c];
+        A.lap[c * n + s] = T(lp[c]);
         eta -= P.b[c] * r[c];
         rt += r[c];
     }
@@ -97,9 +105,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_mu_kernel(AdjArrays A, DevPar
 }
 
 // ---- local transpose of collision, forcing, Psi, friction, force -------------------------
-template <int LAT, int N>
+template <int LAT, int N, class T>
 __global__ void __launch_bounds__(ADJ_THREADS)
-    adj_local_kernel(const double *__restrict__ fbar_next, double *__restrict__ fbar, AdjArrays A, DevParams P) {
+    adj_local_kernel(const T *__restrict__ fbar_next, T *__restrict__ fbar, AdjArrays<T> A, DevParams P) {
     using L = Lat<LAT>;
     constexpr int Q = L::Q, D = L::D;
     const int nx = P.nx, ny = P.ny;
@@ -107,78 +115,80 @@ __global__ void __launch_bounds__(ADJ_THREADS)
     const size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int x = (int)(s % nx), y = (int)(s / nx);
-    const double th = 1.0 / 3.0, omega = P.omega, cg = P.psi_g, cl = P.psi_l;
+    const T th = T(1.0 / 3.0), omega = T(P.omega), cg = T(P.psi_g), cl = T(P.psi_l);
 
-    // ---------- forward recompute at this node
-    double rho[N], u[N][2], gmu[N][2], G[N][2], dphi[N][2], drho[N][2], lap[N], h[2][N], u0[2][N];
-    double W[N][N], M[N][N];
+    // ---------- forward recompute at this node (D phi from the FP64 phi, then rounded to T)
+    T rho[N], u[N][2], gmu[N][2], G[N][2], dphi[N][2], drho[N][2], h[2][N], u0[2][N];
+    T W[N][N], M[N][N];
 #pragma unroll
     for (int c = 0; c < N; ++c) {
-        rho[c] = A.rho[c * n + s];
-        lap[c] = A.lap[c * n + s];
-        grad_g<LAT>(A.phi + c * n, x, y, nx, ny, dphi[c][0], dphi[c][1]);
-        grad_g<LAT>(A.rho + c * n, x, y, nx, ny, drho[c][0], drho[c][1]);
+        rho[c] = T(A.rho[c * n + s]);
+        double px, py, qx, qy;
+        grad_g<LAT>(A.phi + c * n, x, y, nx, ny, px, py);
+        grad_g<LAT>(A.rho + c * n, x, y, nx, ny, qx, qy);
+        dphi[c][0] = T(px), dphi[c][1] = T(py), drho[c][0] = T(qx), drho[c][1] = T(qy);
         for (int a = 0; a < 2; ++a) {
-            u[c][a] = (a < D) ? A.j[(c * D + a) * n + s] / rho[c] : 0.0;
-            gmu[c][a] = (a < D) ? -rho[c] * dphi[c][a] + th * drho[c][a] : 0.0;
+            u[c][a] = (a < D) ? T(A.j[(c * D + a) * n + s] / A.rho[c * n + s]) : T(0);
+            gmu[c][a] = (a < D) ? -rho[c] * dphi[c][a] + th * drho[c][a] : T(0);
             G[c][a] = gmu[c][a];
         }
     }
 #pragma unroll
     for (int c = 0; c < N; ++c)
 #pragma unroll
-        for (int d = 0; d < N; ++d) W[c][d] = (c == d) ? 0.0 : P.lam[c * 4 + d] * rho[c] * rho[d] / (rho[c] + rho[d]);
+        for (int d = 0; d < N; ++d)
+            W[c][d] = (c == d) ? T(0) : T(P.lam[c * 4 + d]) * rho[c] * rho[d] / (rho[c] + rho[d]);
 #pragma unroll
     for (int c = 0; c < N; ++c) {
-        double diag = rho[c];
+        T diag = rho[c];
 #pragma unroll
         for (int d = 0; d < N; ++d) {
-            M[c][d] = -0.5 * W[c][d];
-            diag += 0.5 * W[c][d];
+            M[c][d] = T(-0.5) * W[c][d];
+            diag += T(0.5) * W[c][d];
         }
         M[c][c] = diag;
     }
     // M^{-1} by Gauss-Jordan (symmetric positive definite, N <= 4)
-    double Mi[N][N];
+    T Mi[N][N];
     {
-        double T[N][2 * N];
+        T Tm[N][2 * N];
 #pragma unroll
         for (int c = 0; c < N; ++c)
 #pragma unroll
-            for (int d = 0; d < 2 * N; ++d) T[c][d] = d < N ? M[c][d] : (d - N == c ? 1.0 : 0.0);
+            for (int d = 0; d < 2 * N; ++d) Tm[c][d] = d < N ? M[c][d] : (d - N == c ? T(1) : T(0));
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            double inv = 1.0 / T[k][k];
+            T inv = T(1) / Tm[k][k];
 #pragma unroll
-            for (int d = 0; d < 2 * N; ++d) T[k][d] *= inv;
+            for (int d = 0; d < 2 * N; ++d) Tm[k][d] *= inv;
 #pragma unroll
             for (int r2 = 0; r2 < N; ++r2) {
                 if (r2 == k) continue;
-                double m = T[r2][k];
+                T m = Tm[r2][k];
 #pragma unroll
-                for (int d = 0; d < 2 * N; ++d) T[r2][d] -= m * T[k][d];
+                for (int d = 0; d < 2 * N; ++d) Tm[r2][d] -= m * Tm[k][d];
             }
         }
 #pragma unroll
         for (int c = 0; c < N; ++c)
 #pragma unroll
-            for (int d = 0; d < N; ++d) Mi[c][d] = T[c][N + d];
+            for (int d = 0; d < N; ++d) Mi[c][d] = Tm[c][N + d];
     }
     if constexpr (N > 1) {
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            double rhs[N];
+            T rhs[N];
 #pragma unroll
-            for (int c = 0; c < N; ++c) u0[a][c] = u[c][a] + gmu[c][a] / (2.0 * rho[c]);
+            for (int c = 0; c < N; ++c) u0[a][c] = u[c][a] + gmu[c][a] / (T(2) * rho[c]);
 #pragma unroll
             for (int c = 0; c < N; ++c) {
-                rhs[c] = 0.0;
+                rhs[c] = T(0);
 #pragma unroll
                 for (int d = 0; d < N; ++d) rhs[c] -= W[c][d] * (u0[a][c] - u0[a][d]);
             }
 #pragma unroll
             for (int c = 0; c < N; ++c) {
-                double acc = 0.0;
+                T acc = T(0);
 #pragma unroll
                 for (int d = 0; d < N; ++d) acc += Mi[c][d] * rhs[d];
                 h[a][c] = acc;
@@ -188,57 +198,57 @@ __global__ void __launch_bounds__(ADJ_THREADS)
     }
 
     // ---------- backward
-    double rhob[N], ub[N][2], Gb[N][2];
+    T rhob[N], ub[N][2], Gb[N][2];
 #pragma unroll
     for (int c = 0; c < N; ++c) {
-        rhob[c] = 0.0;
-        ub[c][0] = ub[c][1] = 0.0;
-        Gb[c][0] = Gb[c][1] = 0.0;
-        const double r = rho[c], ux = u[c][0], uy = u[c][1], gx = G[c][0], gy = G[c][1];
-        const double usq = ux * ux + uy * uy;
-        double Sxxb = 0.0, Syyb = 0.0, Sxyb = 0.0;
+        rhob[c] = T(0);
+        ub[c][0] = ub[c][1] = T(0);
+        Gb[c][0] = Gb[c][1] = T(0);
+        const T r = rho[c], ux = u[c][0], uy = u[c][1], gx = G[c][0], gy = G[c][1];
+        const T usq = ux * ux + uy * uy;
+        T Sxxb = T(0), Syyb = T(0), Sxyb = T(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const double cx = L::vx(i), cy = L::vy(i), wi = L::w(i);
+            const T cx = T(L::vx(i)), cy = T(L::vy(i)), wi = T(L::w(i));
             // streaming: post_i(x) went to x + v_i
-            const double pb = fbar_next[(size_t)(c * Q + i) * n + Nb<LAT>::at(x, y, i, nx, ny)];
-            fbar[(size_t)(c * Q + i) * n + s] = (1.0 - omega) * pb;   // d post / d f_i (direct)
-            const double eb = omega * pb;                                 // feq bar
-            const double vu = cx * ux + cy * uy;
-            rhob[c] += eb * wi * (1.0 + 3.0 * vu + 4.5 * vu * vu - 1.5 * usq);
-            ub[c][0] += eb * wi * r * (3.0 * cx + 9.0 * vu * cx - 3.0 * ux);
-            ub[c][1] += eb * wi * r * (3.0 * cy + 9.0 * vu * cy - 3.0 * uy);
+            const T pb = fbar_next[(size_t)(c * Q + i) * n + Nb<LAT>::at(x, y, i, nx, ny)];
+            fbar[(size_t)(c * Q + i) * n + s] = (T(1) - omega) * pb;   // d post / d f_i (direct)
+            const T eb = omega * pb;                                      // feq bar
+            const T vu = cx * ux + cy * uy;
+            rhob[c] += eb * wi * (T(1) + T(3) * vu + T(4.5) * vu * vu - T(1.5) * usq);
+            ub[c][0] += eb * wi * r * (T(3) * cx + T(9) * vu * cx - T(3) * ux);
+            ub[c][1] += eb * wi * r * (T(3) * cy + T(9) * vu * cy - T(3) * uy);
             // F_i = w_i (3 v.G + 4.5 S:(vv - theta I))
-            Gb[c][0] += pb * wi * 3.0 * cx;
-            Gb[c][1] += pb * wi * 3.0 * cy;
-            Sxxb += pb * wi * 4.5 * (cx * cx - th);
+            Gb[c][0] += pb * wi * T(3) * cx;
+            Gb[c][1] += pb * wi * T(3) * cy;
+            Sxxb += pb * wi * T(4.5) * (cx * cx - th);
             if (LAT == 2) {
-                Syyb += pb * wi * 4.5 * (cy * cy - th);
-                Sxyb += pb * wi * 9.0 * cx * cy;
+                Syyb += pb * wi * T(4.5) * (cy * cy - th);
+                Sxyb += pb * wi * T(9) * cx * cy;
             }
         }
         // S_xx = 2 G_x u_x + cg G_x^2/rho + cl Lap;  S_yy likewise;  S_xy = G_x u_y + u_x G_y + cg G_x G_y/rho
-        const double ir = 1.0 / r;
-        Gb[c][0] += Sxxb * (2.0 * ux + 2.0 * cg * gx * ir) + Sxyb * (uy + cg * gy * ir);
-        Gb[c][1] += Syyb * (2.0 * uy + 2.0 * cg * gy * ir) + Sxyb * (ux + cg * gx * ir);
-        ub[c][0] += Sxxb * 2.0 * gx + Sxyb * gy;
-        ub[c][1] += Syyb * 2.0 * gy + Sxyb * gx;
+        const T ir = T(1) / r;
+        Gb[c][0] += Sxxb * (T(2) * ux + T(2) * cg * gx * ir) + Sxyb * (uy + cg * gy * ir);
+        Gb[c][1] += Syyb * (T(2) * uy + T(2) * cg * gy * ir) + Sxyb * (ux + cg * gx * ir);
+        ub[c][0] += Sxxb * T(2) * gx + Sxyb * gy;
+        ub[c][1] += Syyb * T(2) * gy + Sxyb * gx;
         rhob[c] += -(Sxxb * cg * gx * gx + Syyb * cg * gy * gy + Sxyb * cg * gx * gy) * ir * ir;
         A.lapb[c * n + s] = (Sxxb + Syyb) * cl;
     }
     // friction: G = Gmu + rho h,  M h = rhs,  rhs = -L_W u0,  u0 = u + Gmu/(2 rho)
-    double gmub[N][2], Mb[N][N], Wb[N][N];
+    T gmub[N][2], Mb[N][N], Wb[N][N];
 #pragma unroll
     for (int c = 0; c < N; ++c) {
         gmub[c][0] = Gb[c][0];
         gmub[c][1] = Gb[c][1];
 #pragma unroll
-        for (int d = 0; d < N; ++d) Mb[c][d] = Wb[c][d] = 0.0;
+        for (int d = 0; d < N; ++d) Mb[c][d] = Wb[c][d] = T(0);
     }
     if constexpr (N > 1) {
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            double hb[N], rb[N];
+            T hb[N], rb[N];
 #pragma unroll
             for (int c = 0; c < N; ++c) {
                 rhob[c] += h[a][c] * Gb[c][a];
@@ -246,7 +256,7 @@ __global__ void __launch_bounds__(ADJ_THREADS)
             }
 #pragma unroll
             for (int c = 0; c < N; ++c) {
-                double acc = 0.0;
+                T acc = T(0);
 #pragma unroll
                 for (int d = 0; d < N; ++d) acc += Mi[c][d] * hb[d];  // M symmetric
                 rb[c] = acc;
@@ -257,15 +267,15 @@ __global__ void __launch_bounds__(ADJ_THREADS)
                 for (int d = 0; d < N; ++d) Mb[c][d] -= rb[c] * h[a][d];
 #pragma unroll
             for (int c = 0; c < N; ++c) {
-                double u0b = 0.0;
+                T u0b = T(0);
 #pragma unroll
                 for (int d = 0; d < N; ++d) {
                     u0b += W[c][d] * (rb[d] - rb[c]);
                     Wb[c][d] += -rb[c] * (u0[a][c] - u0[a][d]);
                 }
                 ub[c][a] += u0b;
-                gmub[c][a] += u0b / (2.0 * rho[c]);
-                rhob[c] += -u0b * gmu[c][a] / (2.0 * rho[c] * rho[c]);
+                gmub[c][a] += u0b / (T(2) * rho[c]);
+                rhob[c] += -u0b * gmu[c][a] / (T(2) * rho[c] * rho[c]);
             }
         }
 #pragma unroll
@@ -274,7 +284,7 @@ __global__ void __launch_bounds__(ADJ_THREADS)
 #pragma unroll
             for (int d = 0; d < N; ++d) {
                 if (d == c) continue;
-                Wb[c][d] += 0.5 * Mb[c][c] - 0.5 * Mb[c][d];
+                Wb[c][d] += T(0.5) * Mb[c][c] - T(0.5) * Mb[c][d];
             }
         }
 #pragma unroll
@@ -282,8 +292,8 @@ __global__ void __launch_bounds__(ADJ_THREADS)
 #pragma unroll
             for (int d = 0; d < N; ++d) {
                 if (d == c) continue;
-                const double sum = rho[c] + rho[d];
-                const double k = P.lam[c * 4 + d] / (sum * sum);
+                const T sum = rho[c] + rho[d];
+                const T k = T(P.lam[c * 4 + d]) / (sum * sum);
                 rhob[c] += Wb[c][d] * k * rho[d] * rho[d];
                 rhob[d] += Wb[c][d] * k * rho[c] * rho[c];
             }
@@ -291,8 +301,8 @@ __global__ void __launch_bounds__(ADJ_THREADS)
     // u = j / rho;  Gmu = -rho D phi + theta D rho
 #pragma unroll
     for (int c = 0; c < N; ++c) {
-        const double ir = 1.0 / rho[c];
-        double acc = 0.0;
+        const T ir = T(1) / rho[c];
+        T acc = T(0);
         for (int a = 0; a < D; ++a) {
             A.jb[(c * D + a) * n + s] = ub[c][a] * ir;
             acc += ub[c][a] * u[c][a];
@@ -306,8 +316,8 @@ __global__ void __launch_bounds__(ADJ_THREADS)
 }
 
 // ---- mubar = gamma (-div Dphibar); parameter-gradient partials ---------------------------
-template <int LAT, int N>
-__global__ void __launch_bounds__(ADJ_THREADS) adj_mubar_kernel(AdjArrays A, DevParams P) {
+template <int LAT, int N, class T>
+__global__ void __launch_bounds__(ADJ_THREADS) adj_mubar_kernel(AdjArrays<T> A, DevParams P) {
     using L = Lat<LAT>;
     constexpr int D = L::D;
     constexpr int V = 2 * N * N + N;
@@ -323,16 +333,17 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_mubar_kernel(AdjArrays A, Dev
 #pragma unroll
         for (int c = 0; c < N; ++c) {
             // div^T: phibar(x) = -sum_a D_a(Dphibar_a)(x)
-            double dv = 0.0;
-            double gx, gy;
+            T dv = T(0);
+            T gx, gy;
             grad_g<LAT>(A.dphib + (c * D + 0) * n, x, y, nx, ny, gx, gy);
             dv += gx;
             if (D == 2) {
                 grad_g<LAT>(A.dphib + (c * D + 1) * n, x, y, nx, ny, gx, gy);
                 dv += gy;
             }
-            mb[c] = -P.gamma * dv;
-            A.mub[c * n + s] = mb[c];
+            const T mbt = T(-P.gamma) * dv;
+            A.mub[c * n + s] = mbt;
+            mb[c] = (double)mbt;
             r[c] = A.rho[c * n + s];
             eta -= P.b[c] * r[c];
             rt += r[c];
@@ -344,7 +355,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_mubar_kernel(AdjArrays A, Dev
 #pragma unroll
             for (int d = 0; d < N; ++d) {
                 acc[c * N + d] = mb[c] * (-2.0 * r[d]);
-                acc[N * N + c * N + d] = mb[c] * (-A.lap[d * n + s]);
+                acc[N * N + c * N + d] = mb[c] * (-(double)A.lap[d * n + s]);
                 acc[2 * N * N + d] += mb[c] * P.kT *
                                       (r[d] / eta + (c == d ? rt / eta : 0.0) + P.b[c] * rt * r[d] / (eta * eta));
             }
@@ -353,8 +364,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_mubar_kernel(AdjArrays A, Dev
 }
 
 // ---- rhobar and fbar ---------------------------------------------------------------------
-template <int LAT, int N>
-__global__ void __launch_bounds__(ADJ_THREADS) adj_rhobar_kernel(double *__restrict__ fbar, AdjArrays A, DevParams P) {
+template <int LAT, int N, class T>
+__global__ void __launch_bounds__(ADJ_THREADS) adj_rhobar_kernel(T *__restrict__ fbar, AdjArrays<T> A, DevParams P) {
     using L = Lat<LAT>;
     constexpr int Q = L::Q, D = L::D;
     const int nx = P.nx, ny = P.ny;
@@ -366,42 +377,43 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_rhobar_kernel(double *__restr
 #pragma unroll
     for (int c = 0; c < N; ++c) {
         r[c] = A.rho[c * n + s];
-        mb[c] = A.mub[c * n + s];
+        mb[c] = (double)A.mub[c * n + s];
         eta -= P.b[c] * r[c];
         rt += r[c];
     }
     const double ieta = 1.0 / eta;
 #pragma unroll
     for (int d = 0; d < N; ++d) {
-        double rb = A.rhob[d * n + s];
-        // local chemical-potential Jacobian (kT part and the -2a term)
+        // local chemical-potential Jacobian (kT part and the -2a term), in FP64
+        double jt = 0.0;
 #pragma unroll
         for (int c = 0; c < N; ++c) {
             double J = P.kT * ((c == d ? 1.0 / r[c] : 0.0) + (P.b[c] + P.b[d]) * ieta + P.b[c] * P.b[d] * rt * ieta * ieta) -
                        2.0 * P.a[c * 4 + d];
-            rb += mb[c] * J;
+            jt += mb[c] * J;
         }
+        T rb = A.rhob[d * n + s] + T(jt);
         // -kappa Lap rho terms: rhobar^d -= Lap(sum_c kappa_cd mubar^c)
         {
-            const double c0 = [&] {
-                double t = 0.0;
+            const T c0 = [&] {
+                T t = T(0);
 #pragma unroll
-                for (int c = 0; c < N; ++c) t += P.kappa[c * 4 + d] * A.mub[c * n + s];
+                for (int c = 0; c < N; ++c) t += T(P.kappa[c * 4 + d]) * A.mub[c * n + s];
                 return t;
             }();
-            double accl = 0.0;
+            T accl = T(0);
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const size_t nb = Nb<LAT>::at(x, y, i, nx, ny);
-                double t = 0.0;
+                T t = T(0);
 #pragma unroll
-                for (int c = 0; c < N; ++c) t += P.kappa[c * 4 + d] * A.mub[c * n + nb];
-                accl += L::w(i) * (t - c0);
+                for (int c = 0; c < N; ++c) t += T(P.kappa[c * 4 + d]) * A.mub[c * n + nb];
+                accl += T(L::w(i)) * (t - c0);
             }
-            rb -= 6.0 * accl;
+            rb -= T(6) * accl;
         }
         // D rho^T and Lap^T
-        double gx, gy;
+        T gx, gy;
         grad_g<LAT>(A.drhob + (d * D + 0) * n, x, y, nx, ny, gx, gy);
         rb -= gx;
         if (D == 2) {
@@ -409,10 +421,11 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_rhobar_kernel(double *__restr
             rb -= gy;
         }
         rb += lap_g<LAT>(A.lapb + d * n, x, y, nx, ny);
-        const double jbx = A.jb[(d * D + 0) * n + s];
-        const double jby = D == 2 ? A.jb[(d * D + 1) * n + s] : 0.0;
+        const T jbx = A.jb[(d * D + 0) * n + s];
+        const T jby = D == 2 ? A.jb[(d * D + 1) * n + s] : T(0);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) fbar[(size_t)(d * Q + i) * n + s] += rb + L::vx(i) * jbx + L::vy(i) * jby;
+        for (int i = 0; i < Q; ++i)
+            fbar[(size_t)(d * Q + i) * n + s] += rb + T(L::vx(i)) * jbx + T(L::vy(i)) * jby;
     }
 }
 
@@ -424,23 +437,25 @@ __global__ void adj_accum_kernel(const double *__restrict__ step, double *__rest
 }
 
 // fbar_i = rhobar for every i (the loss depends on f only through rho = sum_i f_i)
-__global__ void adj_seed_kernel(const double *__restrict__ rb, double *__restrict__ fb, int N, int Q, size_t n) {
+template <class T>
+__global__ void adj_seed_kernel(const double *__restrict__ rb, T *__restrict__ fb, int N, int Q, size_t n) {
     const size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (s >= n) return;
     for (int c = 0; c < N; ++c)
-        for (int i = 0; i < Q; ++i) fb[(size_t)(c * Q + i) * n + s] = rb[c * n + s];
+        for (int i = 0; i < Q; ++i) fb[(size_t)(c * Q + i) * n + s] = T(rb[c * n + s]);
 }
 
-// f_0 = w_i rho_0 (equilibrium at rest): rhobar_0 = sum_i w_i fbar_0,i
-template <int LAT>
-__global__ void adj_init_transpose_kernel(const double *__restrict__ fb, double *__restrict__ rb, int N, size_t n) {
+// f_0 = w_i rho_0 (equilibrium at rest; with FP32 storage g_0 = w_i (rho_0 - rho_ref), the
+// same transpose): rhobar_0 = sum_i w_i fbar_0,i, summed in FP64
+template <int LAT, class T>
+__global__ void adj_init_transpose_kernel(const T *__restrict__ fb, double *__restrict__ rb, int N, size_t n) {
     using L = Lat<LAT>;
     const size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (s >= n) return;
     for (int c = 0; c < N; ++c) {
         double acc = 0.0;
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) acc += L::w(i) * fb[(size_t)(c * L::Q + i) * n + s];
+        for (int i = 0; i < L::Q; ++i) acc += L::w(i) * (double)fb[(size_t)(c * L::Q + i) * n + s];
         rb[c * n + s] = acc;
     }
 }

@@ -51,10 +51,14 @@ bool finite_all(const double *m, int cnt) {
     return true;
 }
 
-cudaError_t run_step(lb_ctx *c) {
+}  // namespace
+
+// One timestep of the context's lattice, precision and kernel organisation from fin to
+// fout (the forward step of lb_step; also the recompute step of the adjoint rollout).
+cudaError_t lb_ctx_step(lb_ctx *c, const void *fin, void *fout) {
     StepLaunch a;
-    a.fin = c->f[c->cur];
-    a.fout = c->f[c->cur ^ 1];
+    a.fin = fin;
+    a.fout = fout;
     a.P = c->dp;
     a.ncomp = c->p.ncomp;
     a.force = c->p.force_method;
@@ -74,6 +78,10 @@ cudaError_t run_step(lb_ctx *c) {
         default: return d1 ? d1q3_f64_step(a) : d2q9_f64_step(a);
     }
 }
+
+namespace {
+
+cudaError_t run_step(lb_ctx *c) { return lb_ctx_step(c, c->f[c->cur], c->f[c->cur ^ 1]); }
 
 FieldLaunch field_args(lb_ctx *c) {
     FieldLaunch a;
@@ -606,7 +614,7 @@ lb_status lb_destroy(lb_ctx *c) {
     cudaFree(c->diag);
     cudaFree(c->err);
     cudaFree(c->tbl);
-    for (double *q : c->ckpt) cudaFree(q);
+    for (void *q : c->ckpt) cudaFree(q);
     delete c;
     return LB_OK;
 }

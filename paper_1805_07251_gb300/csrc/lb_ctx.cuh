@@ -7,9 +7,9 @@
 #include "lbvdw.h"
 
 struct lb_ctx {
-    // checkpointed rollout for the adjoint (lb_rollout_*): FP64 copies of the state every
-    // ckpt_every steps, and the number of steps recorded
-    std::vector<double *> ckpt;
+    // checkpointed rollout for the adjoint (lb_rollout_*): copies of the state (in its
+    // storage type) every ckpt_every steps, and the number of steps recorded
+    std::vector<void *> ckpt;
     int ckpt_every = 0;
     int64_t rollout_steps = -1;
     lb_params p;
@@ -32,3 +32,5 @@ struct lb_ctx {
     std::string msg;
 };
 
+// One timestep of the context's lattice, precision and kernel organisation (lb_api.cu).
+cudaError_t lb_ctx_step(lb_ctx *c, const void *fin, void *fout);

@@ -24,3 +24,32 @@ def gpu_lib():
     build.build()
     capi.load()
     return capi
+
+
+# Parity bounds applied by the GPU tests, printed in the terminal summary so that every
+# run's log shows which bound each comparison used and what it measured.
+_BOUNDS = []
+
+
+@pytest.fixture
+def parity_bound(request):
+    """check(quantity, measured, bound): assert measured < bound and record both."""
+    name = request.node.nodeid.split("::")[-1]
+
+    def check(quantity, measured, bound):
+        measured, bound = float(measured), float(bound)
+        _BOUNDS.append((name, quantity, measured, bound))
+        assert measured < bound, f"{quantity}: {measured:.3e} is not below the bound {bound:.3e}"
+
+    return check
+
+
+def pytest_terminal_summary(terminalreporter):
+    if not _BOUNDS:
+        return
+    tr = terminalreporter
+    tr.write_sep("-", "parity bounds applied (measured < bound)")
+    for name, quantity, measured, bound in _BOUNDS:
+        tr.write_line(f"{name[:58]:58s} {quantity[:34]:34s} {measured:9.2e} < {bound:9.2e}")
+    worst = max(_BOUNDS, key=lambda b: b[2] / b[3] if b[3] > 0 else 0.0)
+    tr.write_line(f"closest to its bound: {worst[0]} {worst[1]} ({worst[2]:.2e} of {worst[3]:.2e})")

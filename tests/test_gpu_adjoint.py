@@ -1,6 +1,8 @@
 """GPU tests of the adjoint rollout: the hand-written transpose of the fused FP64 step
 against central finite differences (h = 1e-4) of the GPU forward and of the CPU oracle,
-checkpoint invariance, and the torch.autograd.Function wrapper."""
+checkpoint invariance, and the torch.autograd.Function wrapper; the FP32 rollouts (FP32
+storage, FP64 or double-float mu in the forward; FP32 adjoint with FP64 mu) against the
+one-step dot-product identity and against the FP64 gradients."""
 import numpy as np
 import pytest
 
@@ -50,12 +52,12 @@ def oracle_loss(spec, a12, kappa, b, rho0, tgt):
     return float(np.sum((r - tgt) ** 2))
 
 
-def adjoint_grads(spec, rho0, tgt, ckpt):
+def adjoint_grads(spec, rho0, tgt, ckpt, precision="fp64"):
     from paper_1805_07251_gb300 import Simulation, capi
 
     sim = Simulation(lattice=spec["lattice"], nx=spec["nx"], ny=spec["ny"], ncomp=2, tau=spec["tau"],
                      kT=spec["kT"], gamma_mu=spec["gamma_mu"], a=spec["a"], kappa=np.full((2, 2), spec["kappa"]),
-                     lam=spec["lam"], b=spec["b"], precision="fp64")
+                     lam=spec["lam"], b=spec["b"], precision=precision)
     sim.init(rho0)
     capi.lb_rollout_forward(sim.ctx, spec["steps"], ckpt)
     r, _ = sim.moments()
@@ -108,14 +110,14 @@ def test_adjoint_matches_oracle_finite_differences(gpu_lib, lattice):
     assert abs(np.sum(rb0 * v) - fd_r) <= 1e-6 * abs(fd_r)
 
 
-def final_density(spec, a12, rho0):
+def final_density(spec, a12, rho0, precision="fp64"):
     from paper_1805_07251_gb300 import Simulation
 
     a = np.array(spec["a"], float).copy()
     a[0, 1] = a[1, 0] = a12
     sim = Simulation(lattice=spec["lattice"], nx=spec["nx"], ny=spec["ny"], ncomp=2, tau=spec["tau"],
                      kT=spec["kT"], gamma_mu=spec["gamma_mu"], a=a, kappa=np.full((2, 2), spec["kappa"]),
-                     lam=spec["lam"], b=spec["b"], precision="fp64")
+                     lam=spec["lam"], b=spec["b"], precision=precision)
     sim.init(rho0)
     sim.step(spec["steps"])
     r, _ = sim.moments()
@@ -178,3 +180,59 @@ def test_autograd_function(gpu_lib):
     assert abs(a12.grad.item() - (ga[0, 1] + ga[1, 0])) <= 1e-12 * abs(a12.grad.item())
     assert abs(kap.grad.item() - gk.sum()) <= 1e-12 * abs(kap.grad.item())
     assert np.allclose(rho0.grad.numpy(), rb0, rtol=1e-12, atol=0)
+
+
+# ------------------------------------------------------------------ FP32 rollouts
+
+@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32_dfmu"])
+@pytest.mark.parametrize("lattice", ["D1Q3", "D2Q9"])
+def test_fp32_one_step_dot_product(gpu_lib, parity_bound, lattice, precision):
+    # <J v, w> = <v, J^T w> for one step of an FP32-storage context, J^T w from the FP32
+    # adjoint (FP64 mu).  J v comes from Richardson-extrapolated central differences of the
+    # FP64 forward from the same initial densities: the two linearisation points differ by
+    # the FP32 rounding of the stored state, so agreement is bounded by FP32 precision.
+    from paper_1805_07251_gb300 import Simulation, capi
+
+    spec = spec_small(lattice, 1)
+    rho0 = fields(spec)
+    rng = np.random.default_rng(11)
+    v = 1e-2 * rng.normal(0, 1, rho0.shape)
+    w = rng.normal(0, 1, rho0.shape)
+    sim = Simulation(lattice=spec["lattice"], nx=spec["nx"], ny=spec["ny"], ncomp=2, tau=spec["tau"],
+                     kT=spec["kT"], gamma_mu=spec["gamma_mu"], a=spec["a"], kappa=np.full((2, 2), spec["kappa"]),
+                     lam=spec["lam"], b=spec["b"], precision=precision)
+    sim.init(rho0)
+    capi.lb_rollout_forward(sim.ctx, 1, 1)
+    rb0, g = capi.lb_rollout_backward(sim.ctx, w, 2)
+    sim.close()
+    a12 = spec["a"][0, 1]
+    jv = central(lambda t: float(np.sum(final_density(spec, a12, rho0 + t * v) * w)), 0.0, 1e-4)
+    parity_bound("<v, J^T w> vs <J v, w> (rel.)", abs(np.sum(rb0 * v) - jv) / abs(jv), 1e-5)
+    ja = central(lambda t: float(np.sum(final_density(spec, t, rho0) * w)), a12, 1e-3)
+    parity_bound("d<rho_1, w>/d a12 (rel.)", abs((g[1] + g[2]) - ja) / abs(ja), 1e-4)
+
+
+@pytest.mark.parametrize("precision", ["fp32_mixed", "fp32_dfmu"])
+@pytest.mark.parametrize("lattice", ["D1Q3", "D2Q9"])
+def test_fp32_gradients_against_fp64(gpu_lib, parity_bound, lattice, precision):
+    # the FP32 rollout's gradients (FP32 forward and adjoint, FP64 mu) against the FP64
+    # rollout's on the same loss: they differ by the FP32 forward trajectory's distance
+    # from the FP64 one and the FP32 arithmetic of the adjoint; checkpointing must not
+    # change them (the recompute is bitwise the forward)
+    spec = spec_small(lattice, 60)
+    rho0, tgt = fields(spec), target(spec)
+    r64 = adjoint_grads(spec, rho0, tgt, ckpt=25)
+    r32 = adjoint_grads(spec, rho0, tgt, ckpt=25, precision=precision)
+    r32b = adjoint_grads(spec, rho0, tgt, ckpt=7, precision=precision)
+    for u, w in zip(r32, r32b):
+        assert np.array_equal(u, w)
+    rb64, ga64, gk64, gb64 = r64
+    rb32, ga32, gk32, gb32 = r32
+    da = abs((ga32[0, 1] + ga32[1, 0]) - (ga64[0, 1] + ga64[1, 0])) / abs(ga64[0, 1] + ga64[1, 0])
+    dk = abs(gk32.sum() - gk64.sum()) / abs(gk64.sum())
+    db = np.max(np.abs(gb32 - gb64)) / np.max(np.abs(gb64))
+    dr = np.max(np.abs(rb32 - rb64)) / np.max(np.abs(rb64))
+    parity_bound("dL/da12 vs FP64 adjoint (rel.)", da, 1e-3)
+    parity_bound("dL/dkappa vs FP64 adjoint (rel.)", dk, 1e-3)
+    parity_bound("dL/db vs FP64 adjoint (rel. max)", db, 1e-3)
+    parity_bound("dL/drho0 vs FP64 adjoint (rel. max)", dr, 1e-3)
