@@ -54,6 +54,9 @@ class _Params(ctypes.Structure):
         ("b", ctypes.c_double * 4),
         ("force_method", ctypes.c_int),
         ("psi_sign", ctypes.c_double),
+        ("mrt", ctypes.c_int),
+        ("tau_s", ctypes.c_double),
+        ("tau_g", ctypes.c_double),
     ]
 
 
@@ -115,7 +118,7 @@ class Lattice:
     """Plain parameter record for the oracle (no arithmetic of the method)."""
 
     def __init__(self, lattice, nx, ny, ncomp, tau, kT, gamma_mu, a, kappa, lam, b,
-                 force_method=0, psi_sign=-1.0):
+                 force_method=0, psi_sign=-1.0, tau_s=None, tau_g=None):
         self.lattice = {"D1Q3": 1, "D2Q9": 2}.get(lattice, lattice)
         self.nx, self.ny, self.ncomp = int(nx), int(ny), int(ncomp)
         self.q = 3 if self.lattice == 1 else 9
@@ -127,6 +130,10 @@ class Lattice:
         self.b = np.asarray(b, dtype=np.float64).reshape(ncomp)
         self.force_method = int(force_method)
         self.psi_sign = float(psi_sign)
+        # distinct relaxation times of the shear and ghost moments (D2Q9): None = tau (BGK)
+        self.mrt = int(tau_s is not None or tau_g is not None)
+        self.tau_s = float(tau if tau_s is None else tau_s)
+        self.tau_g = float(tau if tau_g is None else tau_g)
 
     def _c(self):
         p = _Params()
@@ -141,6 +148,7 @@ class Lattice:
                 p.lam[c * 4 + cc] = self.lam[c, cc]
         p.force_method = self.force_method
         p.psi_sign = self.psi_sign
+        p.mrt, p.tau_s, p.tau_g = self.mrt, self.tau_s, self.tau_g
         return p
 
     # shapes -------------------------------------------------------------

@@ -18,7 +18,8 @@
  *            as an N x N linear system per node and direction
  *   stage 5  Psi correction (Eq. forceCorrectionsPsi)
  *   stage 6  equilibrium (Eq. feq), forcing populations with the moments of
- *            Sec. III, BGK collision (Eq. BGKcollisionOperator, single tau)
+ *            Sec. III, collision (Eq. BGKcollisionOperator): single tau (BGK), or
+ *            on D2Q9 optionally distinct relaxation times per moment eigenspace
  *   stage 7  streaming (Eq. LBequation), periodic in every direction
  *
  * Readings of the paper taken here, where it is silent or its printed signs
@@ -78,6 +79,13 @@ typedef struct {
     double a[16], kappa[16], lambda[16], b[4];  /* ncomp x ncomp, row major */
     int force_method;     /* 0 = "log" (Eq. forceMuLog), 1 = "nid" (Eq. forceMuId) */
     double psi_sign;      /* sign of Psi in the second forcing moment (-1 default) */
+    /* Collision matrix of Eq. BGKcollisionOperator, diagonal in a moment basis (D2Q9
+     * only; D1Q3 has a single non-conserved moment, so its collision is always BGK):
+     * mrt = 0: one relaxation time tau for every moment (BGK);
+     * mrt = 1: tau for the bulk moment (trace of the second moment), tau_s for the two
+     * shear moments (its traceless part), tau_g for the three ghost moments. */
+    int mrt;
+    double tau_s, tau_g;
 } orc_params;
 
 /* ---- lattices --------------------------------------------------------- */
@@ -115,6 +123,7 @@ static int check_params(const orc_params *p, lattice_t *L) {
     if (get_lattice(p, L) != ORC_OK) return ORC_E_INVALID;
     if (p->nx < 1 || p->ny < 1 || p->ncomp < 1 || p->ncomp > 4) return ORC_E_INVALID;
     if (!(p->tau > 0.5)) return ORC_E_INVALID;
+    if (p->mrt && !(p->tau_s > 0.5 && p->tau_g > 0.5)) return ORC_E_INVALID;
     return ORC_OK;
 }
 
@@ -343,6 +352,14 @@ static int forces(const orc_params *p, const lattice_t *L, const double *rho, co
     return bad ? ORC_E_DOMAIN : ORC_OK;
 }
 
+/* ---- Hermite basis of D1Q3 (and, as products, of D2Q9) at theta = 1/3 ------- */
+
+/* P_0 = 1, P_1 = v, P_2 = v^2 - theta: orthogonal under the D1Q3 weights */
+static double herm(int k, int v) { return k == 0 ? 1.0 : (k == 1 ? (double)v : (double)(v * v) - THETA); }
+
+/* sum_i w_i P_k(v_i)^2 over D1Q3: 1, theta, 2 theta^2 */
+static double herm_norm(int k) { return k == 0 ? 1.0 : (k == 1 ? THETA : 2.0 * THETA * THETA); }
+
 /* ---- one timestep ---------------------------------------------------------- */
 
 typedef struct {
@@ -352,6 +369,7 @@ typedef struct {
 static int step(const orc_params *p, const lattice_t *L, double *f, work_t *w) {
     long n = (long)p->nx * p->ny;
     int N = p->ncomp, Q = L->q, D = L->d;
+    const int mrt = p->mrt && p->lattice == 2;
     int rc = orc_moments(p, f, w->rho, w->mom);                  /* stage 1 */
     if (rc) return rc;
     rc = orc_mu(p, w->rho, w->mu);                               /* stage 2 */
@@ -376,6 +394,19 @@ static int step(const orc_params *p, const lattice_t *L, double *f, work_t *w) {
                     for (int bb = 0; bb < 2; ++bb)
                         Psi[a][bb] = -(1.0 / p->tau) *
                                      ((p->tau - 0.25) * G[a] * G[bb] / r + (a == bb ? lr / 12.0 : 0.0));
+                if (mrt) {
+                    /* distinct relaxation times: the same correction taken per eigenspace
+                     * of the second moment, the trace part (|G|^2/2 I / rho and the
+                     * Laplacian) with the bulk tau, the traceless part of G G / rho with
+                     * tau_s; equal to the line above when tau_s = tau */
+                    double tr = 0.5 * (G[0] * G[0] + G[1] * G[1]);
+                    for (int a = 0; a < 2; ++a)
+                        for (int bb = 0; bb < 2; ++bb) {
+                            double iso = (a == bb ? tr : 0.0);
+                            Psi[a][bb] = -(1.0 / p->tau) * ((p->tau - 0.25) * iso / r + (a == bb ? lr / 12.0 : 0.0))
+                                         - (1.0 / p->tau_s) * (p->tau_s - 0.25) * (G[a] * G[bb] - iso) / r;
+                        }
+                }
                 /* second forcing moment S_ab = G_a u_b + u_a G_b + psi_sign Psi_ab */
                 double S[2][2];
                 for (int a = 0; a < 2; ++a)
@@ -392,32 +423,78 @@ static int step(const orc_params *p, const lattice_t *L, double *f, work_t *w) {
                  * sum to one, which would change the mass by a fixed fraction each
                  * step). */
                 double feq_moving = 0.0, F_moving = 0.0;
+                double feq[9], Fv[9], fv[9], post[9];
                 for (int k = 1; k <= Q; ++k) {
                     const int i = k % Q; /* 1, 2, ..., Q-1, then the rest population 0 */
                     double v[2] = {(double)L->vx[i], (double)L->vy[i]};
                     double vu = v[0] * u[0] + v[1] * u[1];
-                    double feq = r * L->w[i] *
-                                 (1.0 + vu / THETA + vu * vu / (2.0 * THETA * THETA) -
-                                  usq / (2.0 * THETA));
+                    feq[i] = r * L->w[i] *
+                             (1.0 + vu / THETA + vu * vu / (2.0 * THETA * THETA) - usq / (2.0 * THETA));
                     double vG = v[0] * G[0] + v[1] * G[1];
                     double SQ = 0.0;
                     for (int a = 0; a < D; ++a)
                         for (int bb = 0; bb < D; ++bb)
                             SQ += S[a][bb] * (v[a] * v[bb] - (a == bb ? THETA : 0.0));
-                    double Fi = L->w[i] * (vG / THETA + SQ / (2.0 * THETA * THETA));
+                    Fv[i] = L->w[i] * (vG / THETA + SQ / (2.0 * THETA * THETA));
                     if (i == 0) {
-                        feq = r - feq_moving;
-                        Fi = -F_moving;
+                        feq[0] = r - feq_moving;
+                        Fv[0] = -F_moving;
                     } else {
-                        feq_moving += feq;
-                        F_moving += Fi;
+                        feq_moving += feq[i];
+                        F_moving += Fv[i];
                     }
-                    double fi = f[((long)c * Q + i) * n + s];
-                    /* BGK (Eq. BGKcollisionOperator, single relaxation time) */
-                    double post = fi + (feq - fi) / p->tau + Fi;
-                    /* stage 7: streaming, f_i(x + v_i, t + 1) = post-collision f_i(x, t) */
-                    w->fpost[((long)c * Q + i) * n + nb(p, x, y, L->vx[i], L->vy[i])] = post;
+                    fv[i] = f[((long)c * Q + i) * n + s];
                 }
+                if (!mrt) {
+                    /* BGK (Eq. BGKcollisionOperator, single relaxation time) */
+                    for (int i = 0; i < Q; ++i) post[i] = fv[i] + (feq[i] - fv[i]) / p->tau + Fv[i];
+                } else {
+                    /* Eq. BGKcollisionOperator with the collision matrix diagonal in the
+                     * D2Q9 Hermite basis H_a(v) = P_ax(v_x) P_ay(v_y), P in {1, v, v^2 -
+                     * theta}, orthogonal under the weights with norms N_a = sum_i w_i H_a^2:
+                     *   Omega_i = w_i sum_a (1/tau_a) H_a(v_i) m_a / N_a,
+                     *   m_a = sum_j H_a(v_j) (f_j^eq - f_j).
+                     * 1/tau_a: conserved moments (1, v_x, v_y; m_a = 0) and the bulk
+                     * combination H_xx + H_yy take tau; H_xx - H_yy and H_xy take tau_s;
+                     * H_xxy, H_xyy, H_xxyy take tau_g.  The rest population again comes
+                     * from the zeroth-moment condition sum_i Omega_i = 0. */
+                    double m[3][3];
+                    for (int ax = 0; ax < 3; ++ax)
+                        for (int ay = 0; ay < 3; ++ay) {
+                            double acc = 0.0;
+                            for (int i = 0; i < Q; ++i)
+                                acc += herm(ax, L->vx[i]) * herm(ay, L->vy[i]) * (feq[i] - fv[i]);
+                            m[ax][ay] = acc;
+                        }
+                    /* bulk / shear split of the H_xx (ax = 2, ay = 0) and H_yy moments */
+                    double bulk = 0.5 * (m[2][0] + m[0][2]) / p->tau;
+                    double shear = 0.5 * (m[2][0] - m[0][2]) / p->tau_s;
+                    double om_moving = 0.0;
+                    for (int k = 1; k <= Q; ++k) {
+                        const int i = k % Q;
+                        double acc = 0.0;
+                        for (int ax = 0; ax < 3; ++ax)
+                            for (int ay = 0; ay < 3; ++ay) {
+                                double Ha = herm(ax, L->vx[i]) * herm(ay, L->vy[i]);
+                                double Na = herm_norm(ax) * herm_norm(ay);
+                                double rate;
+                                if (ax + ay <= 1) rate = 1.0 / p->tau;          /* conserved */
+                                else if (ax == 1 && ay == 1) rate = 1.0 / p->tau_s;
+                                else if (ax + ay == 2) continue;                /* H_xx, H_yy below */
+                                else rate = 1.0 / p->tau_g;                     /* ghosts */
+                                acc += rate * Ha * m[ax][ay] / Na;
+                            }
+                        double hxx = herm(2, L->vx[i]), hyy = herm(2, L->vy[i]);
+                        acc += (bulk * (hxx + hyy) + shear * (hxx - hyy)) / herm_norm(2);
+                        double om = L->w[i] * acc;
+                        if (i == 0) om = -om_moving;
+                        else om_moving += om;
+                        post[i] = fv[i] + om + Fv[i];
+                    }
+                }
+                /* stage 7: streaming, f_i(x + v_i, t + 1) = post-collision f_i(x, t) */
+                for (int i = 0; i < Q; ++i)
+                    w->fpost[((long)c * Q + i) * n + nb(p, x, y, L->vx[i], L->vy[i])] = post[i];
             }
     memcpy(f, w->fpost, sizeof(double) * (size_t)N * Q * n);
     return ORC_OK;
