@@ -54,12 +54,16 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--tile", default=None, help="D2Q9 tile as TXxTY (default: the library's)")
-    ap.add_argument("--kernel", choices=["auto", "tiles", "strips"], default="auto",
+    ap.add_argument("--kernel", choices=["auto", "tiles", "strips", "ws"], default="auto",
                     help="organisation of the step kernel (default: the library's choice)")
     ap.add_argument("--segments", type=int, default=0, help="strips: row segments per strip (0 = library's)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched-sweep measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-rollout measurement")
     ap.add_argument("--no-c4", action="store_true", help="skip the four-component measurement")
+    ap.add_argument("--adjoint-steps", type=int, default=0,
+                    help="adjoint rollouts: steps of the rollout (0: the workload's 2000)")
+    ap.add_argument("--no-fd", action="store_true",
+                    help="adjoint rollouts: skip the finite-difference checks (profiling runs)")
     ap.add_argument("--only", choices=["fp32_dfmu", "fp32_mixed", "fp32", "fp64", "sweep", "c4", "adjoint", "c1"],
                     default=None,
                     help="time one path only (profiling runs): no e2e, no cpu baseline")
@@ -70,7 +74,8 @@ def parse(argv=None):
 # step kernel, from an ncu capture of this script (the profile file named beside it).  The
 # value holds for the kernel sources whose digest is recorded with it and is reported as
 # null once they change.
-KERNEL_SOURCES = ("lb_kernels.cuh", "lb_lane.cuh", "lb_mu.cuh", "lb_tu.cuh", "lb_launch.cuh", "lb_d2q9_df.cu")
+KERNEL_SOURCES = ("lb_kernels.cuh", "lb_lane.cuh", "lb_mu.cuh", "lb_tu.cuh", "lb_launch.cuh", "lb_d2q9_df.cu",
+                  "lb_ws.cuh")
 TRAFFIC = {"fp32_dfmu": {"digest": "255b9ab2346c543830fd3b767b93eca8c1f2a067b99c7efcd7c78041ca35bec0",
                          "bytes": 107393280, "warp_instructions": 28700672, "issue_active": 0.577,
                          "fma_pipe_active": 0.509,
@@ -267,12 +272,15 @@ def run_reference(args):
 def time_sweep(torch, dev, precision, steps, warmup, dist):
     """Batched sweep (workload c3): 256 D1Q3 + 128 D2Q9 independent runs advanced together
     by CUDA-graph replays; D2Q9 tile from the autotuner.  The state (1.8 GB per step)
-    exceeds the L2, so no flush is needed between steps."""
+    exceeds the L2, so no flush is needed between steps.  Before timing, the campaign's
+    pre-scan (3000 steps) re-tunes runs that leave the density domain (wider interfaces,
+    lower gamma_mu), as the paper's campaigns did."""
     import lbinputs
-    from paper_1805_07251_gb300.batch import Batch, autotune
+    from paper_1805_07251_gb300.batch import Batch, autotune, prescan
 
-    recs = lbinputs.sweep_runs()
     p = lbinputs.base_params("c1")
+    recs, scan_fail = prescan(lbinputs.sweep_runs(), lbinputs.sweep_fields, p["a"], p["b"], p["kappa"], p["lam"], 2,
+                              precision=precision, device=dev, stream=torch.cuda.current_stream(dev).cuda_stream)
     fields = [lbinputs.sweep_fields(r) for r in recs]
     b = Batch(recs, p["a"], p["b"], p["kappa"], p["lam"], 2, precision=precision, device=dev,
               stream=torch.cuda.current_stream(dev).cuda_stream)
@@ -292,6 +300,7 @@ def time_sweep(torch, dev, precision, steps, warmup, dist):
            "runs": len(recs), "d1q3_runs": sum(r["lattice"] == "D1Q3" for r in recs),
            "d2q9_runs": sum(r["lattice"] == "D2Q9" for r in recs), "component_nodes": cn,
            "tile": "x".join(map(str, tile)) if tile else None, "unstable_runs_after_warmup_and_timed": unstable,
+           "retuned_runs": sum(1 for r in recs if r.get("retuned")), "prescan_failures": scan_fail,
            "dtype": DTYPES[precision], "gpu_launches": launches,
            "note": "one CUDA-graph replay per 32 timesteps: D1Q3 runs resident in shared memory, "
                    "D2Q9 runs as one tile-list launch per timestep"}
@@ -439,7 +448,7 @@ class MemPeak:
         return self.free0 - self.low
 
 
-def time_adjoint(torch, dev):
+def time_adjoint(torch, dev, steps_override=0, fd=True):
     """Workload c5: D2Q9, 2 components, 512^2, config-2 mixture and temperature with
     a12 = 0.75, 2000 steps checkpointed every 100; loss = sum (rho_T - rho_target)^2 with
     the target from the FP64 forward at a12 = 0.8.  Times one gradient (forward with
@@ -453,7 +462,7 @@ def time_adjoint(torch, dev):
     from paper_1805_07251_gb300 import Simulation, capi
 
     p = lbinputs.base_params("c5")
-    n, steps, ckpt = p["nx"], p["steps"], 100
+    n, steps, ckpt = p["nx"], (steps_override or p["steps"]), 100
     rho0 = lbinputs.fields("c5")
     st = torch.cuda.current_stream(dev).cuda_stream
 
@@ -495,6 +504,13 @@ def time_adjoint(torch, dev):
                     bwd=t2 - t1, mem=mp.peak_bytes)
 
     g64 = gradient("fp64")
+    if not fd:
+        out = {"steps": steps, "s_per_gradient": g64["total"], "backward_s": g64["bwd"],
+               "peak_device_bytes": g64["mem"]}
+        for precision in ("fp32_mixed", "fp32_dfmu"):
+            g = gradient(precision)
+            out[precision] = {"s_per_gradient": g["total"], "backward_s": g["bwd"], "peak_device_bytes": g["mem"]}
+        return out
     fa, fa0 = richardson(lambda x: loss(x, 0.1), 0.75, 1e-4)
     fk, fk0 = richardson(lambda x: loss(0.75, x), 0.1, 1e-4)
     fr, fr0 = richardson(lambda t: loss(0.75, 0.1, rho0 + t * v), 0.0, 1e-4)
@@ -532,7 +548,7 @@ def time_path(torch, Simulation, kw, rho, precision, steps, warmup, flush, dev):
     each step, L2 flushed before each step outside the events."""
     stream = torch.cuda.current_stream(dev)
     sim = Simulation(precision=precision, device=dev, stream=stream.cuda_stream, tile=TILE,
-                     kernel=KERNEL if precision != "fp64" else "auto", segments=SEGMENTS, **kw)
+                     kernel=kernel_for(precision), segments=SEGMENTS, **kw)
     sim.init(rho)
     for _ in range(warmup):
         flush.zero_()
@@ -541,6 +557,14 @@ def time_path(torch, Simulation, kw, rho, precision, steps, warmup, flush, dev):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     launches0 = sim.launches
     return sim, ev, launches0, stream
+
+
+def kernel_for(precision):
+    """The requested kernel organisation where it applies to the precision, else the
+    library's choice (strips: FP32 storage; warp-specialised tiles: FP32-class mu)."""
+    if precision == "fp64" or (KERNEL == "ws" and precision == "fp32_mixed"):
+        return "auto"
+    return KERNEL
 
 
 TILE = None
@@ -600,7 +624,7 @@ def main():
         elif args.only == "c1":
             out = time_c1(torch, dev, 10000)
         else:
-            out = time_adjoint(torch, dev)
+            out = time_adjoint(torch, dev, args.adjoint_steps, fd=not args.no_fd)
         if rank == 0:
             print(json.dumps({"only": args.only, **out}), flush=True)
         if dist is not None:
@@ -712,7 +736,8 @@ def main():
                      "frac": head["achieved"] / peak_gbs, "traffic": traffic_of(HEAD)[0],
                      "traffic_profile": traffic_of(HEAD)[1], "peak_kind": peak_kind,
                      "kernel": "%s<D2Q9, N=2, %s, %s>" % (
-                         "lb_strip_kernel" if head["kernel"].startswith("strips") else "lb_step_kernel",
+                         {"strips": "lb_strip_kernel", "ws": "lb_step_ws_kernel"}.get(head["kernel"].split()[0],
+                                                                                      "lb_step_kernel"),
                          head["kernel"].split()[1], HEAD),
                      "alg_bytes_per_launch": head["alg_bytes"],
                      "limiter": limiter_of(HEAD, head["alg_bytes"], peak_gbs)},

@@ -61,7 +61,7 @@
 extern "C" {
 #endif
 
-#define LBVDW_ABI 2
+#define LBVDW_ABI 3
 
 typedef enum {
     LB_OK = 0,
@@ -101,10 +101,15 @@ typedef enum { LB_FORCE_LOG = 0, LB_FORCE_NID = 1 } lb_force_method;
  *                     mbarrier completion) while the current rows are collided.
  *                     Needs nx % tile_x == 0 and ny % tile_y == 0, with
  *                     (tile_x, tile_y) = (32, 8) for 1-2 components, (32, 4) for 3-4.
- *   LB_KERNEL_AUTO    tiles (measured faster on GB300: 44.5k against 27.8k component-
- *                     MLUPS for 2 components at 1024^2; the strips' shared-memory
- *                     staging leaves two CTAs, 18 warps, per SM). */
-typedef enum { LB_KERNEL_AUTO = 0, LB_KERNEL_TILES = 1, LB_KERNEL_STRIPS = 2 } lb_kernel_kind;
+ *   LB_KERNEL_WS      (D2Q9, two components, LB_FP32_DFMU or LB_FP32, 32 x 8 tiles)
+ *                     persistent warp-specialised tiles: per CTA, 4 loader warps stage
+ *                     the next tile (populations, densities, momenta) in double-buffered
+ *                     shared memory while 8 compute warps run mu and the collision of the
+ *                     current one.  Bitwise the results of LB_KERNEL_TILES.
+ *   LB_KERNEL_AUTO    tiles (measured faster on GB300 than the strips: 44.5k against
+ *                     27.8k component-MLUPS for 2 components at 1024^2; the strips'
+ *                     shared-memory staging leaves two CTAs, 18 warps, per SM). */
+typedef enum { LB_KERNEL_AUTO = 0, LB_KERNEL_TILES = 1, LB_KERNEL_STRIPS = 2, LB_KERNEL_WS = 3 } lb_kernel_kind;
 
 typedef struct {
     uint32_t abi;        /* must equal LBVDW_ABI */
@@ -133,6 +138,19 @@ typedef struct {
     int32_t segments;    /* strips: row segments per strip (0 = enough CTAs to fill the
                             GPU once); ignored by tiles */
     void *stream;        /* cudaStream_t for every launch and copy; NULL = legacy default */
+    /* Collision matrix of Eq. BGKcollisionOperator, diagonal in the D2Q9 Hermite moment
+     * basis (D2Q9 only, tile kernel with 32 x 8 tiles; 0 = tau, i.e. BGK):
+     *   tau_shear  relaxation time of the two shear moments (traceless second moment):
+     *              kinematic viscosity theta (tau_shear - 1/2); 1/2 < tau_shear <= tau
+     *              (larger values are unstable with the Psi correction);
+     *   tau_ghost  relaxation time of the three ghost moments (third and fourth order),
+     *              > 1/2.
+     * The bulk moment (trace) keeps tau.  The Psi correction (Eq. forceCorrectionsPsi)
+     * is taken per eigenspace: trace with tau, traceless part of G G / rho with
+     * tau_shear.  With tau_shear = tau the stationary states are exactly those of BGK
+     * for any tau_ghost; tau_shear < tau shifts coexisting densities by O(1e-3). */
+    double tau_shear;
+    double tau_ghost;
 } lb_params;
 
 typedef struct lb_ctx lb_ctx;
@@ -238,7 +256,7 @@ lb_status lb_rollout_backward(lb_ctx *ctx, const double *rho_bar_T, double *rho_
 
 /* ---- batched independent runs (a phase-diagram sweep) --------------------------------
  * Many independent runs that share the mixture (ncomp, a, b, kappa, lambda, tau, force
- * method, precision) but differ in lattice, size, kT and gamma_mu advance together on
+ * method, precision) but differ in lattice, size, kT, gamma_mu and a kappa scale advance together on
  * one GPU.  Every run follows exactly the arithmetic of the same run advanced alone
  * through lb_create/lb_step (bitwise equal results).  D2Q9 runs: one kernel launch per
  * timestep over a flat list of tiles of all runs.  D1Q3 runs (2 <= nx <= 4096): one CTA
@@ -249,6 +267,9 @@ typedef struct {
     int32_t nx, ny;
     double kT;        /* this run's thermodynamic temperature */
     double gamma_mu;  /* this run's gamma_mu */
+    double kappa_scale; /* this run's kappa^{cc'} = kappa_scale * shared kappa^{cc'} (0 = 1):
+                           a wider interface, the stabilisation of deep quenches (Sec. VI);
+                           equilibrium bulk phases do not depend on kappa */
 } lb_run_desc;
 
 typedef struct lb_batch lb_batch;

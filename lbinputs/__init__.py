@@ -198,8 +198,10 @@ def sweep_runs(n_d1=256, n_d2=128, with_phases=True):
 
 def sweep_fields(rec):
     """Seeded initial densities [c][y][x] of one sweep run: a slab of the liquid phase
-    between tanh edges (width 2) in the gas phase, sized by the lever rule so that the
-    mean is rec['mean'], plus uniform noise in +-1e-3; one-phase runs: the mean plus noise."""
+    between tanh edges (width rec['width'], default 2) in the gas phase, sized by the lever
+    rule so that the mean is rec['mean'], plus uniform noise in +-1e-3; one-phase runs: the
+    mean plus noise."""
+    width = float(rec.get("width", 2.0))
     g = np.random.default_rng(rec["seed"] + 10 ** 6)
     nx, ny = rec["nx"], rec["ny"]
     mean = np.asarray(rec["mean"])
@@ -210,7 +212,7 @@ def sweep_fields(rec):
         xs = np.arange(nx, dtype=np.float64)
         lo = nx * (0.5 - phi / 2) - 0.5
         hi = nx * (0.5 + phi / 2) - 0.5
-        s = 0.5 * (np.tanh((xs - lo) / 2.0) - np.tanh((xs - hi) / 2.0))
+        s = 0.5 * (np.tanh((xs - lo) / width) - np.tanh((xs - hi) / width))
         rho = np.stack([gas[c] + (liq[c] - gas[c]) * s for c in range(2)])[:, None, :]
         rho = np.broadcast_to(rho, (2, ny, nx)).copy()
     else:

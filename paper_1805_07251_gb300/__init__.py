@@ -18,7 +18,8 @@ __all__ = ["capi", "Simulation", "make_params"]
 _LATTICES = {"D1Q3": capi.LB_D1Q3, "D2Q9": capi.LB_D2Q9}
 _PRECISIONS = {"fp64": capi.LB_FP64, "fp32_mixed": capi.LB_FP32_MIXED, "fp32_dfmu": capi.LB_FP32_DFMU, "fp32": capi.LB_FP32}
 _FORCES = {"log": capi.LB_FORCE_LOG, "nid": capi.LB_FORCE_NID}
-_KERNELS = {"auto": capi.LB_KERNEL_AUTO, "tiles": capi.LB_KERNEL_TILES, "strips": capi.LB_KERNEL_STRIPS}
+_KERNELS = {"auto": capi.LB_KERNEL_AUTO, "tiles": capi.LB_KERNEL_TILES, "strips": capi.LB_KERNEL_STRIPS,
+            "ws": capi.LB_KERNEL_WS}
 
 
 def _current_stream(device):
@@ -33,9 +34,11 @@ def _current_stream(device):
 
 def make_params(lattice, nx, ny, ncomp, tau, kT, gamma_mu, a, kappa, lam, b,
                 precision="fp64", force="log", device=0, stream=None, tile=None,
-                rho_ref=None, check_every=0, kernel="auto", segments=0):
+                rho_ref=None, check_every=0, kernel="auto", segments=0, tau_shear=0.0, tau_ghost=0.0):
     """Fill an ``lb_params`` struct from Python values (matrices as N x N).  ``kernel``:
-    "auto", "tiles" or "strips" (organisation of the step kernel, see lb_kernel_kind)."""
+    "auto", "tiles" or "strips" (organisation of the step kernel, see lb_kernel_kind).
+    ``tau_shear`` / ``tau_ghost``: relaxation times of the shear and ghost moments (D2Q9;
+    0 = tau, the BGK collision)."""
     p = capi.lb_default_params()
     p.lattice = _LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
     p.nx, p.ny, p.ncomp = int(nx), int(ny), int(ncomp)
@@ -61,6 +64,7 @@ def make_params(lattice, nx, ny, ncomp, tau, kT, gamma_mu, a, kappa, lam, b,
         p.tile_x, p.tile_y = int(tile[0]), int(tile[1])
     p.kernel = _KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
     p.segments = int(segments)
+    p.tau_shear, p.tau_ghost = float(tau_shear), float(tau_ghost)
     if stream is None:
         stream = _current_stream(device)
     p.stream = stream
@@ -128,7 +132,7 @@ class Simulation:
     def kernel(self):
         """Organisation of the step kernel chosen by lb_create: ("tiles" or "strips", tile)."""
         p = capi.lb_get_params(self.ctx)
-        kind = {capi.LB_KERNEL_TILES: "tiles", capi.LB_KERNEL_STRIPS: "strips"}[p.kernel]
+        kind = {capi.LB_KERNEL_TILES: "tiles", capi.LB_KERNEL_STRIPS: "strips", capi.LB_KERNEL_WS: "ws"}[p.kernel]
         return kind, (p.tile_x, p.tile_y)
 
     def close(self):

@@ -26,14 +26,15 @@ class Batch:
 
     def __init__(self, runs, a, b, kappa, lam, ncomp, tau=1.0, precision="fp32_dfmu", force="log",
                  device=0, stream=None, tile=None):
-        """runs: list of dicts with lattice ("D1Q3"/"D2Q9"), nx, ny, kT, gamma_mu."""
+        """runs: list of dicts with lattice ("D1Q3"/"D2Q9"), nx, ny, kT, gamma_mu and an
+        optional kappa_scale (this run's kappa = kappa_scale * kappa; default 1)."""
         self.shared = make_params("D2Q9", 2, 2, ncomp, tau, 1.0, 1.0, a, kappa, lam, b, precision=precision,
                                   force=force, device=device, stream=stream, tile=tile)
         self.ncomp = ncomp
         self.runs = [dict(r) for r in runs]
         lat = {"D1Q3": capi.LB_D1Q3, "D2Q9": capi.LB_D2Q9}
-        self.b = capi.lb_batch_create(self.shared, [(lat[r["lattice"]], r["nx"], r["ny"], r["kT"], r["gamma_mu"])
-                                                     for r in self.runs])
+        self.b = capi.lb_batch_create(self.shared, [(lat[r["lattice"]], r["nx"], r["ny"], r["kT"], r["gamma_mu"],
+                                                      r.get("kappa_scale", 0.0)) for r in self.runs])
 
     def nodes(self, k):
         return self.runs[k]["nx"] * self.runs[k]["ny"]
@@ -79,6 +80,50 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# The campaign's automatic re-tuning of a run that leaves the density domain (Sec. VI: deep
+# quenches were stabilised by widening interfaces -- larger kappa, which the bulk phases do
+# not depend on -- and lowering gamma_mu): each retry multiplies kappa by KAPPA_STEP,
+# divides gamma_mu by the same factor (the interface relation gamma_0 = 1 / (6 kappa rho_l))
+# and widens the initial tanh profile by sqrt(KAPPA_STEP) (the interface width grows as
+# sqrt(kappa)).
+KAPPA_STEP = 4.0
+
+
+def retune(rec):
+    """A run record with the next stabilisation step applied."""
+    r = dict(rec)
+    r["kappa_scale"] = r.get("kappa_scale", 1.0) * KAPPA_STEP
+    r["gamma_mu"] = r["gamma_mu"] / KAPPA_STEP
+    r["width"] = r.get("width", 2.0) * KAPPA_STEP ** 0.5
+    r["retuned"] = r.get("retuned", 0) + 1
+    return r
+
+
+def prescan(runs, fields_of, a, b, kappa, lam, ncomp, steps=3000, rounds=2, **batch_kw):
+    """Scan every run for ``steps`` timesteps in one batch; runs that leave the density
+    domain are re-tuned (``retune``) and scanned again, up to ``rounds`` times.  Returns
+    the run records to use and the number of runs still failing the scan.  ``fields_of``
+    maps a run record to its initial densities."""
+    recs = [dict(r) for r in runs]
+    todo = list(range(len(recs)))
+    for rnd in range(rounds + 1):
+        if not todo:
+            break
+        sub = [recs[k] for k in todo]
+        bt = Batch(sub, a, b, kappa, lam, ncomp, **batch_kw)
+        bt.init([fields_of(r) for r in sub])
+        bt.step(steps)
+        err = bt.errors()
+        bt.close()
+        failed = [k for k, e in zip(todo, err) if e]
+        if rnd == rounds:
+            return recs, len(failed)
+        for k in failed:
+            recs[k] = retune(recs[k])
+        todo = failed
+    return recs, 0
 
 
 def _gpu_name(device):

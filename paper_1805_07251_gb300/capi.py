@@ -16,12 +16,12 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "liblbvdw.so")
 
-LBVDW_ABI = 2
+LBVDW_ABI = 3
 LB_OK, LB_E_INVALID, LB_E_NOMEM, LB_E_CUDA, LB_E_DOMAIN, LB_E_TIMEOUT, LB_E_STATE = range(7)
 LB_D1Q3, LB_D2Q9 = 1, 2
 LB_FP64, LB_FP32_MIXED, LB_FP32_DFMU, LB_FP32 = 0, 1, 2, 3
 LB_FORCE_LOG, LB_FORCE_NID = 0, 1
-LB_KERNEL_AUTO, LB_KERNEL_TILES, LB_KERNEL_STRIPS = 0, 1, 2
+LB_KERNEL_AUTO, LB_KERNEL_TILES, LB_KERNEL_STRIPS, LB_KERNEL_WS = 0, 1, 2, 3
 
 
 class lb_run_desc(ctypes.Structure):
@@ -31,6 +31,7 @@ class lb_run_desc(ctypes.Structure):
         ("ny", ctypes.c_int32),
         ("kT", ctypes.c_double),
         ("gamma_mu", ctypes.c_double),
+        ("kappa_scale", ctypes.c_double),
     ]
 
 
@@ -58,6 +59,8 @@ class lb_params(ctypes.Structure):
         ("kernel", ctypes.c_int32),
         ("segments", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
+        ("tau_shear", ctypes.c_double),
+        ("tau_ghost", ctypes.c_double),
     ]
 
 
@@ -272,10 +275,12 @@ def _bcheck(b, rc, what):
 
 
 def lb_batch_create(shared, runs):
-    """runs: sequence of (lattice, nx, ny, kT, gamma_mu)."""
+    """runs: sequence of (lattice, nx, ny, kT, gamma_mu[, kappa_scale])."""
     arr = (lb_run_desc * len(runs))()
-    for k, (lat, nx, ny, kT, g) in enumerate(runs):
+    for k, run in enumerate(runs):
+        lat, nx, ny, kT, g = run[:5]
         arr[k].lattice, arr[k].nx, arr[k].ny, arr[k].kT, arr[k].gamma_mu = int(lat), int(nx), int(ny), kT, g
+        arr[k].kappa_scale = float(run[5]) if len(run) > 5 else 0.0
     out = ctypes.c_void_p()
     rc = load().lb_batch_create(ctypes.byref(shared), arr, len(runs), ctypes.byref(out))
     if rc != LB_OK:

@@ -168,10 +168,11 @@ extern "C" {
 lb_status lb_rollout_forward(lb_ctx *c, int64_t nsteps, int32_t ckpt_every) {
     if (!c || nsteps < 1 || ckpt_every < 1) return LB_E_INVALID;
     if (c->poisoned || !c->has_state) return rfail(c, LB_E_STATE, "fields not initialised or context poisoned");
-    if (c->p.force_method != LB_FORCE_LOG ||
+    if (c->p.force_method != LB_FORCE_LOG || lb_ctx_mrt(c) ||
         (c->p.precision != LB_FP64 && c->p.precision != LB_FP32_MIXED && c->p.precision != LB_FP32_DFMU))
         return rfail(c, LB_E_INVALID,
-                     "the adjoint rollout needs the log force and FP64, FP32_MIXED or FP32_DFMU precision");
+                     "the adjoint rollout needs the log force, the BGK collision and FP64, FP32_MIXED or "
+                     "FP32_DFMU precision");
     DeviceGuard dg(c->p.device);
     if (!dg.ok()) return rfail(c, LB_E_CUDA, "cudaSetDevice");
     for (void *p : c->ckpt) cudaFree(p);

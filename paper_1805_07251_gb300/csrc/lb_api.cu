@@ -53,6 +53,12 @@ bool finite_all(const double *m, int cnt) {
 
 }  // namespace
 
+// Whether relaxation times other than tau were asked for (the moment-space collision).
+bool lb_ctx_mrt(const lb_ctx *c) {
+    const double t = c->p.tau, ts = c->p.tau_shear, tg = c->p.tau_ghost;
+    return (ts != 0.0 && ts != t) || (tg != 0.0 && tg != t);
+}
+
 // One timestep of the context's lattice, precision and kernel organisation from fin to
 // fout (the forward step of lb_step; also the recompute step of the adjoint rollout).
 cudaError_t lb_ctx_step(lb_ctx *c, const void *fin, void *fout) {
@@ -61,13 +67,14 @@ cudaError_t lb_ctx_step(lb_ctx *c, const void *fin, void *fout) {
     a.fout = fout;
     a.P = c->dp;
     a.ncomp = c->p.ncomp;
-    a.force = c->p.force_method;
+    a.force = c->p.force_method | (lb_ctx_mrt(c) ? 2 : 0);
     a.tile_x = c->p.tile_x;
     a.tile_y = c->p.tile_y;
     a.kernel = c->p.kernel;
     a.segs = c->p.segments;
     a.stream = c->stream;
     const bool d1 = c->p.lattice == LB_D1Q3;
+    if (a.kernel == LB_KERNEL_WS) return c->p.precision == LB_FP32 ? d2q9_f32mu_ws(a) : d2q9_df_ws(a);
     if (a.kernel == LB_KERNEL_STRIPS)
         return c->p.precision == LB_FP32_MIXED ? d2q9_tbl_strip(a)
                                                : (c->p.precision == LB_FP32 ? d2q9_f32mu_strip(a) : d2q9_df_strip(a));
@@ -230,6 +237,13 @@ void make_dev_params(const lb_params &p, DevParams &d, unsigned *err, const LogT
     d.omc_f = (float)d.omc;
     d.lam_fr = p.lambda[1] / (1.0 + 0.5 * p.lambda[1]);
     d.lam_fr_f = (float)d.lam_fr;
+    const double ts = p.tau_shear > 0.0 ? p.tau_shear : p.tau, tg = p.tau_ghost > 0.0 ? p.tau_ghost : p.tau;
+    d.omega_s = 1.0 / ts;
+    d.omega_g = 1.0 / tg;
+    d.psi_s = (ts - 0.25) / ts;
+    d.omega_s_f = (float)d.omega_s;
+    d.omega_g_f = (float)d.omega_g;
+    d.psi_s_f = (float)d.psi_s;
     const long double ln2 = strtold(LN2_DIGITS, nullptr);
     d.ln2_hi_f = (float)ln2;
     d.ln2_lo_f = (float)(ln2 - (long double)d.ln2_hi_f);
@@ -305,7 +319,20 @@ lb_status lb_create(const lb_params *p, lb_ctx **out) {
             if (cc != c && p->lambda[c * 4 + cc] < 0.0) return LB_E_INVALID;
     }
     if (p->check_every < 0) return LB_E_INVALID;
-    if (p->kernel < LB_KERNEL_AUTO || p->kernel > LB_KERNEL_STRIPS || p->segments < 0) return LB_E_INVALID;
+    // moment-space collision: 1/2 < tau_shear <= tau (0 = tau), tau_ghost > 1/2 (0 = tau);
+    // D2Q9 tiles of 32 x 8 only
+    if (!std::isfinite(p->tau_shear) || !std::isfinite(p->tau_ghost)) return LB_E_INVALID;
+    if (p->tau_shear != 0.0 && !(p->tau_shear > 0.5 && p->tau_shear <= p->tau)) return LB_E_INVALID;
+    if (p->tau_ghost != 0.0 && !(p->tau_ghost > 0.5)) return LB_E_INVALID;
+    const bool mrt = (p->tau_shear != 0.0 && p->tau_shear != p->tau) || (p->tau_ghost != 0.0 && p->tau_ghost != p->tau);
+    if (mrt && (p->lattice != LB_D2Q9 || p->kernel == LB_KERNEL_STRIPS ||
+                !((p->tile_x == 0 && p->tile_y == 0) || (p->tile_x == 32 && p->tile_y == 8))))
+        return LB_E_INVALID;
+    if (p->kernel < LB_KERNEL_AUTO || p->kernel > LB_KERNEL_WS || p->segments < 0) return LB_E_INVALID;
+    if (p->kernel == LB_KERNEL_WS &&
+        (p->lattice != LB_D2Q9 || N != 2 || (p->precision != LB_FP32_DFMU && p->precision != LB_FP32) ||
+         !((p->tile_x == 0 && p->tile_y == 0) || (p->tile_x == 32 && p->tile_y == 8))))
+        return LB_E_INVALID;
 
     lb_ctx *c = new (std::nothrow) lb_ctx;
     if (!c) return LB_E_NOMEM;
@@ -318,7 +345,11 @@ lb_status lb_create(const lb_params *p, lb_ctx **out) {
     if (kind == LB_KERNEL_AUTO) kind = LB_KERNEL_TILES;
     c->p.kernel = kind;
     bool tile_ok;
-    if (kind == LB_KERNEL_STRIPS) {
+    if (kind == LB_KERNEL_WS) {
+        c->p.tile_x = 32;
+        c->p.tile_y = 8;
+        tile_ok = true;
+    } else if (kind == LB_KERNEL_STRIPS) {
         if (no_tile) {
             c->p.tile_x = STRIP_TX;
             c->p.tile_y = strip_ty(N);

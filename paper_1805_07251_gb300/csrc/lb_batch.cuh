@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(RESIDENT_THREADS)
                 rho[c] = s_rho[c * RH + ex];
                 lap[c] = lap_at<1, R>(s_rho + c * RH, ex, 0, RH);
                 grad_phi<1, R, MT>(s_phi + c * PH, mx, 0, PH, P, gpx[c], gpy[c]);
-                if constexpr (FORCE == 0) grad_at<1, R>(s_rho + c * RH, ex, 0, RH, grx[c], gry[c]);
+                if constexpr (!Flags<FORCE>::nid) grad_at<1, R>(s_rho + c * RH, ex, 0, RH, grx[c], gry[c]);
                 else grx[c] = gry[c] = (R)0;
                 R acc;
 #pragma unroll

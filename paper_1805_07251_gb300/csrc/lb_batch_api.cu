@@ -199,6 +199,10 @@ lb_status lb_batch_create(const lb_params *shared, const lb_run_desc *runs, int3
         return LB_E_INVALID;
     if (shared->force_method != LB_FORCE_LOG && shared->force_method != LB_FORCE_NID) return LB_E_INVALID;
     if (!(shared->tau > 0.5)) return LB_E_INVALID;
+    // batches run the BGK collision: relaxation times other than tau are single-run only
+    if ((shared->tau_shear != 0.0 && shared->tau_shear != shared->tau) ||
+        (shared->tau_ghost != 0.0 && shared->tau_ghost != shared->tau))
+        return LB_E_INVALID;
     for (int c = 0; c < N; ++c) {
         if (!(shared->b[c] > 0.0)) return LB_E_INVALID;
         for (int cc = 0; cc < N; ++cc)
@@ -226,7 +230,8 @@ lb_status lb_batch_create(const lb_params *shared, const lb_run_desc *runs, int3
         const lb_run_desc &d = runs[r];
         bool ok = (d.lattice == LB_D1Q3 && d.ny == 1 && d.nx >= 2 && d.nx <= RESIDENT_MAX_L) ||
                   (d.lattice == LB_D2Q9 && d.nx >= 2 && d.ny >= 2);
-        ok = ok && d.kT > 0.0 && d.gamma_mu > 0.0 && std::isfinite(d.kT) && std::isfinite(d.gamma_mu);
+        ok = ok && d.kT > 0.0 && d.gamma_mu > 0.0 && std::isfinite(d.kT) && std::isfinite(d.gamma_mu) &&
+             d.kappa_scale >= 0.0 && std::isfinite(d.kappa_scale);
         if (!ok) {
             delete b;
             return LB_E_INVALID;
@@ -281,6 +286,8 @@ lb_status lb_batch_create(const lb_params *shared, const lb_run_desc *runs, int3
         p.ny = runs[r].ny;
         p.kT = runs[r].kT;
         p.gamma_mu = runs[r].gamma_mu;
+        if (runs[r].kappa_scale > 0.0)
+            for (int k = 0; k < 16; ++k) p.kappa[k] = shared->kappa[k] * runs[r].kappa_scale;
         make_dev_params(p, b->hparams[r], b->d_err + r, b->d_tbl);
     }
     if (cudaMemcpy(b->d_tbl, &h, sizeof h, cudaMemcpyHostToDevice) != cudaSuccess ||

@@ -34,3 +34,6 @@ struct lb_ctx {
 
 // One timestep of the context's lattice, precision and kernel organisation (lb_api.cu).
 cudaError_t lb_ctx_step(lb_ctx *c, const void *fin, void *fout);
+
+// Whether the context uses the moment-space collision (relaxation times other than tau).
+bool lb_ctx_mrt(const lb_ctx *c);

@@ -5,4 +5,5 @@
 #define LBVDW_MU MU_DF
 #define LBVDW_NAME d2q9_df
 #define LBVDW_STRIPS 1
+#define LBVDW_WS 1
 #include "lb_tu.cuh"

@@ -5,4 +5,5 @@
 #define LBVDW_MU MU_F32
 #define LBVDW_NAME d2q9_f32mu
 #define LBVDW_STRIPS 1
+#define LBVDW_WS 1
 #include "lb_tu.cuh"

@@ -54,6 +54,19 @@ struct DevParams {
     double omc, lam_fr;
     float omc_f, lam_fr_f;
     float ln2_hi_f, ln2_lo_f;  // ln 2 as a double-float (the df logarithm)
+    // moment-space collision (D2Q9, FORCE bit 1): relaxation rates of the shear and ghost
+    // moments (the bulk moment keeps omega), and the Psi coefficient of the traceless part
+    // of G G / rho, (tau_s - 1/4) / tau_s (psi_g stays that of the trace part)
+    double omega_s, omega_g, psi_s;
+    float omega_s_f, omega_g_f, psi_s_f;
+};
+
+// The FORCE template flag: bit 0 selects the "nid" force (Eq. forceMuId; clear: the
+// "log" force, Eq. forceMuLog), bit 1 the moment-space collision with distinct
+// relaxation times (D2Q9; clear: BGK).
+template <int FORCE> struct Flags {
+    static constexpr bool nid = (FORCE & 1) != 0;
+    static constexpr bool mrt = (FORCE & 2) != 0;
 };
 
 // a parameter in the compute type R: the double value or its precomputed float copy
@@ -294,7 +307,7 @@ __device__ __forceinline__ DF<V> mu_df_lanes(V r, V lin, DF<V> b, df ieta, df rt
     if (!ok) lg = DF<V>{zero, zero};
     const DF<V> m = df_add(lg, df_mul_u(df_splat(rte, r), b));
     DF<V> ph = df_add_f(m, v_mul(lin, vs(-P.ikT_f, r)));
-    if constexpr (FORCE == 1) {
+    if constexpr (Flags<FORCE>::nid) {
         DF<V> lr = df_log(DF<V>{r, zero}, s_t, P.ln2_hi_f, P.ln2_lo_f);
         if (!ok) lr = DF<V>{zero, zero};
         ph = df_add(ph, df_neg(df_mul_u(lr, df_splat(df{P.cnid_hi, P.cnid_lo}, r))));
@@ -306,7 +319,7 @@ template <class V, int FORCE>
 __device__ __forceinline__ V mu_f32_lanes(V r, V lin, V b, float ieta, float rte, const DevParams &P) {
     const V lg = v_log(v_mul(r, vs(ieta, r)));
     V ph = v_fma(lin, vs(-P.ikT_f, r), v_fma(b, vs(rte, r), lg));
-    if constexpr (FORCE == 1) ph = v_fma(v_log(r), vs(-P.cnid_hi, r), ph);
+    if constexpr (Flags<FORCE>::nid) ph = v_fma(v_log(r), vs(-P.cnid_hi, r), ph);
     return ph;
 }
 
@@ -395,7 +408,7 @@ __device__ __forceinline__ bool mu_node(const R (&r)[N], const R (&lin)[N], cons
         for (int c = 0; c < N; ++c) {
             double m = P.kT * (log(r[c] * ieta) + P.b[c] * rt * ieta) - lin[c];
             double ph = P.gamma * m;
-            if constexpr (FORCE == 1) ph -= (1.0 / 3.0) * log(r[c]);
+            if constexpr (Flags<FORCE>::nid) ph -= (1.0 / 3.0) * log(r[c]);
             phi[c] = ph;
         }
     } else if constexpr (MU == MU_TBL) {
@@ -417,7 +430,7 @@ __device__ __forceinline__ bool mu_node(const R (&r)[N], const R (&lin)[N], cons
                                        P.tbl->ln2_lo_d)
                            : 0.0;
             double ph = fma(P.gkT, fma(P.b[c], rte, lg), -P.gamma * (double)lin[c]);
-            if constexpr (FORCE == 1)
+            if constexpr (Flags<FORCE>::nid)
                 ph -= (1.0 / 3.0) * (ok ? log64_tbl((double)r[c], t, t + LOG_TBL, t + 2 * LOG_TBL, P.tbl->ln2_hi_d,
                                                      P.tbl->ln2_lo_d)
                                         : 0.0);
@@ -490,7 +503,7 @@ __device__ __forceinline__ bool mu_node(const R (&r)[N], const R (&lin)[N], cons
 template <int FORCE, class V>
 __device__ __forceinline__ void gain_lane(V rho, V gpx, V gpy, V grx, V gry, V jx, V jy, V &Gx, V &Gy, V &ir, V &ux,
                                           V &uy) {
-    if constexpr (FORCE == 0) {
+    if constexpr (!Flags<FORCE>::nid) {
         Gx = v_fma(v_neg(rho), gpx, v_mul(grx, vc<V>(1.0 / 3.0)));
         Gy = v_fma(v_neg(rho), gpy, v_mul(gry, vc<V>(1.0 / 3.0)));
     } else {
@@ -578,6 +591,81 @@ __device__ __forceinline__ void bgk_lane(V r, V u, V v, V gx, V gy, V lapc, V ir
 #pragma unroll
     for (int i = 1; i < Q; ++i) before = v_add(before, g[i]);
     post[0] = v_sub(before, moved);
+}
+
+// One opposite pair (i, ip = -i) of the moment-space collision with forcing (D2Q9).  The
+// relaxation Omega_i = w_i [Axx H_xx + Ayy H_yy + Axy H_xy + Bxxy H_xxy + Bxyy H_xyy +
+// Bq H_xxyy](v_i) (amplitudes already divided by the norms of the Hermite polynomials) has
+// a part even in v (orders 2 and 4) and an odd part (order 3); the forcing F = C +- D is
+// that of bgk_pair.  post = g + Omega + F.
+template <int I, class V>
+__device__ __forceinline__ void mrt_pair(V Sxx, V Syy, V Sxy, V gx, V gy, V Axx, V Ayy, V Axy, V Bxxy, V Bxyy,
+                                         V Bq, V gi, V gip, V &pi, V &pip) {
+    using L = Lat<2>;
+    constexpr int CX = L::vx(I), CY = L::vy(I);
+    constexpr double W = L::w(I), TH = 1.0 / 3.0;
+    constexpr double hxx = CX * CX - TH, hyy = CY * CY - TH, hxy = CX * CY;
+    constexpr double hxxy = hxx * CY, hxyy = CX * hyy, hq = hxx * hyy;
+    V even = v_mul(v_fma(Sxx, vc<V>(4.5), Axx), vc<V>(W * hxx));
+    even = v_fma(v_fma(Syy, vc<V>(4.5), Ayy), vc<V>(W * hyy), even);
+    if constexpr (CX * CY != 0) even = v_fma(v_fma(Sxy, vc<V>(9.0), Axy), vc<V>(W * hxy), even);
+    even = v_fma(Bq, vc<V>(W * hq), even);
+    V odd = v_mul(dir_dot<CX, CY>(gx, gy), vc<V>(3.0 * W));
+    if constexpr (CY != 0) odd = v_fma(Bxxy, vc<V>(W * hxxy), odd);
+    if constexpr (CX != 0) odd = v_fma(Bxyy, vc<V>(W * hxyy), odd);
+    pi = v_add(gi, v_add(even, odd));
+    pip = v_add(gip, v_sub(even, odd));
+}
+
+// Moment-space collision with forcing of one D2Q9 component lane (Eq. BGKcollisionOperator
+// with the collision matrix diagonal in the Hermite basis H_a = P_ax(v_x) P_ay(v_y),
+// P in {1, v, v^2 - theta}, norms N = 1, theta, 2 theta^2 per factor): the bulk moment
+// H_xx + H_yy relaxes with omega (ob), the shear moments H_xx - H_yy and H_xy with
+// omega_s (os), the ghost moments H_xxy, H_xyy, H_xxyy with omega_g (og); conserved
+// moments are untouched.  -Psi per eigenspace: the trace of G G / rho with cgb =
+// (tau - 1/4)/tau and the Laplacian term, its traceless part with cgs = (tau_s - 1/4)/tau_s.
+// The rest population takes what is left of the node's mass, as in bgk_lane.
+template <class V>
+__device__ __forceinline__ void mrt_lane(V r, V u, V v, V gx, V gy, V lapc, V ir, V ob, V os, V og, V cgb, V cgs,
+                                         V cl, const V (&g)[9], V (&post)[9]) {
+    const V cp = v_mul(v_add(cgb, cgs), vc<V>(0.5)), cm = v_mul(v_sub(cgb, cgs), vc<V>(0.5));
+    const V gxx = v_mul(v_mul(gx, gx), ir), gyy = v_mul(v_mul(gy, gy), ir);
+    const V cll = v_mul(cl, lapc);
+    const V Sxx = v_fma(gx, v_add(u, u), v_fma(cp, gxx, v_fma(cm, gyy, cll)));
+    const V Syy = v_fma(gy, v_add(v, v), v_fma(cm, gxx, v_fma(cp, gyy, cll)));
+    const V Sxy = v_fma(gx, v, v_fma(u, gy, v_mul(v_mul(cgs, ir), v_mul(gx, gy))));
+    // Hermite moments of the stored populations (the rest equilibrium w rho_ref has none
+    // beyond order zero, so deviations give those of f)
+    const V ax = v_add(g[1], g[3]), ay = v_add(g[2], g[4]);
+    const V dsum = v_add(v_add(g[5], g[6]), v_add(g[7], g[8]));
+    const V s0 = v_add(g[0], v_add(v_add(ax, ay), dsum));
+    const V Pxx = v_fma(s0, vc<V>(-1.0 / 3.0), v_add(ax, dsum));
+    const V Pyy = v_fma(s0, vc<V>(-1.0 / 3.0), v_add(ay, dsum));
+    const V Pxy = v_sub(v_add(g[5], g[7]), v_add(g[6], g[8]));
+    const V Qxxy = v_fma(v_sub(v_add(g[5], g[6]), v_add(g[7], g[8])), vc<V>(2.0 / 3.0),
+                         v_mul(v_sub(g[2], g[4]), vc<V>(-1.0 / 3.0)));
+    const V Qxyy = v_fma(v_sub(v_add(g[5], g[8]), v_add(g[6], g[7])), vc<V>(2.0 / 3.0),
+                         v_mul(v_sub(g[1], g[3]), vc<V>(-1.0 / 3.0)));
+    const V Rq = v_fma(dsum, vc<V>(4.0 / 9.0), v_fma(v_add(ax, ay), vc<V>(-2.0 / 9.0), v_mul(g[0], vc<V>(1.0 / 9.0))));
+    // m^eq - m: the equilibrium's second moments are rho u u, its ghost moments zero
+    const V ru = v_mul(r, u), rv = v_mul(r, v);
+    const V dxx = v_fma(ru, u, v_neg(Pxx)), dyy = v_fma(rv, v, v_neg(Pyy)), dxy = v_fma(ru, v, v_neg(Pxy));
+    const V bulk = v_mul(v_add(dxx, dyy), v_mul(ob, vc<V>(2.25)));   // omega (dxx + dyy) / 2 / (2 theta^2)
+    const V shear = v_mul(v_sub(dxx, dyy), v_mul(os, vc<V>(2.25)));
+    const V Axx = v_add(bulk, shear), Ayy = v_sub(bulk, shear);
+    const V Axy = v_mul(dxy, v_mul(os, vc<V>(9.0)));                 // / theta^2
+    const V Bxxy = v_mul(Qxxy, v_mul(og, vc<V>(-13.5)));             // / (2 theta^3)
+    const V Bxyy = v_mul(Qxyy, v_mul(og, vc<V>(-13.5)));
+    const V Bq = v_mul(Rq, v_mul(og, vc<V>(-20.25)));                // / (4 theta^4)
+    mrt_pair<1>(Sxx, Syy, Sxy, gx, gy, Axx, Ayy, Axy, Bxxy, Bxyy, Bq, g[1], g[3], post[1], post[3]);
+    mrt_pair<2>(Sxx, Syy, Sxy, gx, gy, Axx, Ayy, Axy, Bxxy, Bxyy, Bq, g[2], g[4], post[2], post[4]);
+    mrt_pair<5>(Sxx, Syy, Sxy, gx, gy, Axx, Ayy, Axy, Bxxy, Bxyy, Bq, g[5], g[7], post[5], post[7]);
+    mrt_pair<6>(Sxx, Syy, Sxy, gx, gy, Axx, Ayy, Axy, Bxxy, Bxyy, Bq, g[6], g[8], post[6], post[8]);
+    V moved = v_add(post[1], post[3]);
+    moved = v_add(moved, v_add(post[2], post[4]));
+    moved = v_add(moved, v_add(post[5], post[7]));
+    moved = v_add(moved, v_add(post[6], post[8]));
+    post[0] = v_sub(s0, moved);
 }
 
 // Friction of two components with the implicit u-hat: (D + L/2) h = -L u0, G^f = D h per
@@ -706,11 +794,18 @@ __device__ __forceinline__ void collide_pairs(const float2 (&rho)[NP], const flo
         }
     }
 #pragma unroll
-    for (int q = 0; q < NP; ++q)
-        bgk_lane<LAT, float2>(rho[q], ux[q], uy[q], Gx[q], Gy[q], lap[q], ir[q],
-                              make_float2(P.rho_ref_f[2 * q], P.rho_ref_f[2 * q + 1]),
-                              make_float2(P.omega_f, P.omega_f), make_float2(P.omc_f, P.omc_f),
-                              make_float2(P.psi_g_f, P.psi_g_f), make_float2(P.psi_l_f, P.psi_l_f), g[q], post[q]);
+    for (int q = 0; q < NP; ++q) {
+        if constexpr (Flags<FORCE>::mrt && LAT == 2)
+            mrt_lane<float2>(rho[q], ux[q], uy[q], Gx[q], Gy[q], lap[q], ir[q], make_float2(P.omega_f, P.omega_f),
+                             make_float2(P.omega_s_f, P.omega_s_f), make_float2(P.omega_g_f, P.omega_g_f),
+                             make_float2(P.psi_g_f, P.psi_g_f), make_float2(P.psi_s_f, P.psi_s_f),
+                             make_float2(P.psi_l_f, P.psi_l_f), g[q], post[q]);
+        else
+            bgk_lane<LAT, float2>(rho[q], ux[q], uy[q], Gx[q], Gy[q], lap[q], ir[q],
+                                  make_float2(P.rho_ref_f[2 * q], P.rho_ref_f[2 * q + 1]),
+                                  make_float2(P.omega_f, P.omega_f), make_float2(P.omc_f, P.omc_f),
+                                  make_float2(P.psi_g_f, P.psi_g_f), make_float2(P.psi_l_f, P.psi_l_f), g[q], post[q]);
+    }
 }
 
 // One node of phase 3, N components (arrays over c); an even number of FP32 components goes
@@ -758,9 +853,14 @@ __device__ __forceinline__ void collide_node(const R (&rho)[N], const R (&lap)[N
         const R omega = pv<R>(P.omega, P.omega_f), omc = pv<R>(P.omc, P.omc_f);
         const R cg = pv<R>(P.psi_g, P.psi_g_f), cl = pv<R>(P.psi_l, P.psi_l_f);
 #pragma unroll
-        for (int c = 0; c < N; ++c)
-            bgk_lane<LAT, R>(rho[c], ux[c], uy[c], Gx[c], Gy[c], lap[c], ir[c], pv<R>(P.rho_ref[c], P.rho_ref_f[c]),
-                             omega, omc, cg, cl, g[c], post[c]);
+        for (int c = 0; c < N; ++c) {
+            if constexpr (Flags<FORCE>::mrt && LAT == 2)
+                mrt_lane<R>(rho[c], ux[c], uy[c], Gx[c], Gy[c], lap[c], ir[c], omega, pv<R>(P.omega_s, P.omega_s_f),
+                            pv<R>(P.omega_g, P.omega_g_f), cg, pv<R>(P.psi_s, P.psi_s_f), cl, g[c], post[c]);
+            else
+                bgk_lane<LAT, R>(rho[c], ux[c], uy[c], Gx[c], Gy[c], lap[c], ir[c],
+                                 pv<R>(P.rho_ref[c], P.rho_ref_f[c]), omega, omc, cg, cl, g[c], post[c]);
+        }
     }
 }
 
@@ -948,14 +1048,14 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
         rho[q] = sr[e];
         if constexpr (LAT == 1) {
             lap[q] = lap_d1q3(rho[q], sr[e + 1], sr[e - 1]);
-            grx[q] = FORCE == 0 ? grad_d1q3(sr[e + 1], sr[e - 1]) : vc<float2>(0.0);
+            grx[q] = !Flags<FORCE>::nid ? grad_d1q3(sr[e + 1], sr[e - 1]) : vc<float2>(0.0);
             gry[q] = vc<float2>(0.0);
             gpx[q] = v_mul(phi_diff2(phi_at(m + 1), phi_at(m - 1)), vs(P.gkt2_f, rho[q]));
             gpy[q] = vc<float2>(0.0);
         } else {
             const Nbr9<float2> nb = nbr9(sr + e, EX);
             lap[q] = lap_d2q9(nb);
-            if constexpr (FORCE == 0) grad_d2q9(nb, grx[q], gry[q]);
+            if constexpr (!Flags<FORCE>::nid) grad_d2q9(nb, grx[q], gry[q]);
             else grx[q] = gry[q] = vc<float2>(0.0);
             grad_d2q9_diff(phi_diff2(phi_at(m + 1), phi_at(m - 1)), phi_diff2(phi_at(m + MX), phi_at(m - MX)),
                            phi_diff2(phi_at(m + MX + 1), phi_at(m - MX - 1)),  // NE - SW
@@ -1101,7 +1201,7 @@ __device__ __forceinline__ void step_tile(const S *__restrict__ fin, S *__restri
         rho[c] = s_rho[c][ey * EX + ex];
         lap[c] = lap_at<LAT, R>(s_rho[c], ex, ey, EX);
         grad_phi<LAT, R, MT>(s_phi[c], mx, my, MX, P, gpx[c], gpy[c]);
-        if constexpr (FORCE == 0) grad_at<LAT, R>(s_rho[c], ex, ey, EX, grx[c], gry[c]);
+        if constexpr (!Flags<FORCE>::nid) grad_at<LAT, R>(s_rho[c], ex, ey, EX, grx[c], gry[c]);
         else grx[c] = gry[c] = (R)0;
     }
     R gr[N][Q], post[N][Q];

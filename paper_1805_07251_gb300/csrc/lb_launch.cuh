@@ -55,6 +55,8 @@ cudaError_t d2q9_f32mu_step(const StepLaunch &a);
 cudaError_t d2q9_tbl_strip(const StepLaunch &a);
 cudaError_t d2q9_df_strip(const StepLaunch &a);
 cudaError_t d2q9_f32mu_strip(const StepLaunch &a);
+cudaError_t d2q9_df_ws(const StepLaunch &a);
+cudaError_t d2q9_f32mu_ws(const StepLaunch &a);
 
 // field launchers: one per lattice and storage type (double / float)
 #define LBVDW_DECLARE_FIELDS(NAME)                         \

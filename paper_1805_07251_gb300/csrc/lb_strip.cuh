@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(StripLayout<N, TX, TY, MU>::NT, 2)
                 const int ex = col + 2;
                 rho[c] = rb[rm * RW + ex];
                 lap[c] = lap_rows<R>(rb + rs * RW, rb + rm * RW, rb + rn * RW, ex);
-                if constexpr (FORCE == 0) grad_rows<R>(rb + rs * RW, rb + rm * RW, rb + rn * RW, ex, grx[c], gry[c]);
+                if constexpr (!Flags<FORCE>::nid) grad_rows<R>(rb + rs * RW, rb + rm * RW, rb + rn * RW, ex, grx[c], gry[c]);
                 else grx[c] = gry[c] = (R)0;
                 const MT *pb = s_phi + (size_t)c * RING * MW;
                 grad_phi_rows<R, MT>(pb + rs * MW, pb + rm * MW, pb + rn * MW, col + 1, P, gpx[c], gpy[c]);

@@ -7,6 +7,9 @@
 #ifdef LBVDW_STRIPS
 #include "lb_strip.cuh"
 #endif
+#ifdef LBVDW_WS
+#include "lb_ws.cuh"
+#endif
 
 namespace lbvdw {
 
@@ -37,9 +40,19 @@ cudaError_t step_n(const StepLaunch &a) {
     return cudaErrorInvalidValue;
 }
 
+// a.force: bit 0 the "nid" force, bit 1 the moment-space collision (D2Q9, 32 x 8 tiles)
 template <int TX, int TY>
 cudaError_t step_f(const StepLaunch &a) {
-    return a.force == 1 ? step_n<TX, TY, 1>(a) : step_n<TX, TY, 0>(a);
+    switch (a.force) {
+        case 0: return step_n<TX, TY, 0>(a);
+        case 1: return step_n<TX, TY, 1>(a);
+        case 2:
+        case 3:
+            if constexpr (LATV == 2 && TX == 32 && TY == 8)
+                return a.force == 2 ? step_n<TX, TY, 2>(a) : step_n<TX, TY, 3>(a);
+            break;
+    }
+    return cudaErrorInvalidConfiguration;
 }
 
 unsigned field_grid(const DevParams &P) {
@@ -144,8 +157,43 @@ cudaError_t strip_n(const StepLaunch &a) {
 cudaError_t LBVDW_CAT(LBVDW_NAME, _strip)(const StepLaunch &a) {
     if (!strip_shape_ok(a.P.nx, a.P.ny, a.ncomp) || a.tile_x != STRIP_TX || a.tile_y != strip_ty(a.ncomp))
         return cudaErrorInvalidConfiguration;
+    if (a.force & ~1) return cudaErrorInvalidConfiguration;
     return a.force == 1 ? strip_n<1>(a) : strip_n<0>(a);
 }
+
+#ifdef LBVDW_WS
+namespace {
+
+// Persistent warp-specialised tiles (lb_ws.cuh): as many CTAs as fit on the GPU at once,
+// each walking every gridDim.x-th tile.
+template <int FORCE>
+cudaError_t ws_one(const StepLaunch &a) {
+    using Lay = WsLayout<MUV>;
+    auto kern = lb_step_ws_kernel<FORCE, MUV>;
+    static int cache[64];  // one per instantiation, i.e. per kernel
+    const int slots = strip_slots(kern, WS_THREADS, Lay::bytes, cache);
+    if (slots < 0) return cudaErrorInvalidConfiguration;
+    const int tiles_x = (a.P.nx + WS_TX - 1) / WS_TX, tiles_y = (a.P.ny + WS_TY - 1) / WS_TY;
+    const int ntiles = tiles_x * tiles_y;
+    const int grid = slots < ntiles ? slots : ntiles;
+    kern<<<grid, WS_THREADS, Lay::bytes, a.stream>>>(static_cast<const float *>(a.fin), static_cast<float *>(a.fout),
+                                                      a.P, tiles_x, ntiles);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t LBVDW_CAT(LBVDW_NAME, _ws)(const StepLaunch &a) {
+    if (a.ncomp != 2 || a.tile_x != WS_TX || a.tile_y != WS_TY) return cudaErrorInvalidConfiguration;
+    switch (a.force) {
+        case 0: return ws_one<0>(a);
+        case 1: return ws_one<1>(a);
+        case 2: return ws_one<2>(a);
+        case 3: return ws_one<3>(a);
+    }
+    return cudaErrorInvalidConfiguration;
+}
+#endif  // LBVDW_WS
 
 #endif  // LBVDW_STRIPS
 

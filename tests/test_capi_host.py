@@ -54,7 +54,8 @@ def test_status_strings_and_defaults(lib):
     assert capi.status_str(99) == "LB_E_UNKNOWN"
     p = capi.lb_default_params()
     assert p.abi == capi.LBVDW_ABI and p.tau == 1.0 and p.ncomp == 2 and p.lattice == capi.LB_D2Q9
-    assert ctypes.sizeof(capi.lb_params) == 8 * 4 + 8 * 3 + 8 * (16 * 3 + 8) + 4 * 6 + 8
+    assert ctypes.sizeof(capi.lb_params) == 8 * 4 + 8 * 3 + 8 * (16 * 3 + 8) + 4 * 6 + 8 + 8 * 2
+    assert p.tau_shear == 0.0 and p.tau_ghost == 0.0
 
 
 def test_null_arguments_are_rejected_without_cuda(lib):
@@ -112,3 +113,38 @@ def test_batches_reject_the_fp32_mu_precision_without_cuda(lib):
     out = ctypes.c_void_p()
     assert lib.lb_batch_create(ctypes.byref(p), runs, 1, ctypes.byref(out)) == capi.LB_E_INVALID
     assert lib.lb_batch_create(None, runs, 1, ctypes.byref(out)) == capi.LB_E_INVALID
+
+
+def test_relaxation_times_are_validated_without_cuda(lib):
+    # the moment-space collision: 1/2 < tau_shear <= tau, tau_ghost > 1/2, D2Q9 tiles of
+    # 32 x 8 only; batches run BGK.  Each case fails validation before any CUDA call.
+    from paper_1805_07251_gb300 import capi
+
+    def base():
+        p = capi.lb_default_params()
+        p.b[0] = p.b[1] = 0.3
+        p.tau = 1.0
+        return p
+
+    out = ctypes.c_void_p()
+    for ts, tg in ((1.2, 0.0), (0.5, 0.0), (0.0, 0.5), (float("nan"), 0.0), (0.7, float("inf"))):
+        p = base()
+        p.tau_shear, p.tau_ghost = ts, tg
+        assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID
+    p = base()
+    p.tau_shear = 0.7
+    p.lattice, p.ny = capi.LB_D1Q3, 1                    # no shear moments in D1Q3
+    assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID
+    p = base()
+    p.tau_ghost = 0.8
+    p.tile_x, p.tile_y = 64, 4
+    assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID
+    p = base()
+    p.tau_shear = 0.7
+    p.precision, p.kernel = capi.LB_FP32_DFMU, capi.LB_KERNEL_STRIPS
+    assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID
+    p = base()
+    p.tau_shear = 0.7
+    runs = (capi.lb_run_desc * 1)()
+    runs[0].lattice, runs[0].nx, runs[0].ny, runs[0].kT, runs[0].gamma_mu = capi.LB_D2Q9, 64, 64, 1.0 / 3.0, 0.1
+    assert lib.lb_batch_create(ctypes.byref(p), runs, 1, ctypes.byref(out)) == capi.LB_E_INVALID

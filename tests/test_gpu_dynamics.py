@@ -67,3 +67,91 @@ def test_gpu_interdiffusion_follows_maxwell_stefan_fick_law(gpu_lib, parity_boun
             ro, _ = L.moments(f)
             worst = max(worst, abs(_amplitude(ro, k, x) - amps[t - 1]) / amps[t - 1])
         parity_bound("amplitude vs oracle (rel.)", worst, 1e-9)
+
+
+# ------------------------------------------------------------ moment-space collision
+
+def _mrt_pair(precision, tau_s, tau_g, nx, ny, kT=None, **over):
+    from paper_1805_07251_gb300 import Simulation
+    import lbinputs
+
+    p = lbinputs.base_params("c2")
+    kw = lbinputs.lib_kwargs(p, **over)
+    kw["nx"], kw["ny"] = nx, ny
+    if kT is not None:
+        kw["kT"] = kT
+    sim = Simulation(precision=precision, tau_shear=tau_s, tau_ghost=tau_g, **kw)
+    orc = oracle.Lattice("D2Q9", nx, ny, 2, kw["tau"], kw["kT"], kw["gamma_mu"], kw["a"], kw["kappa"], kw["lam"],
+                         kw["b"], tau_s=tau_s, tau_g=tau_g)
+    return sim, orc
+
+
+@pytest.mark.parametrize("tau_s,tau_g", [(0.7, 0.9), (1.0, 0.6), (0.55, 1.0)])
+def test_mrt_fp64_trajectory_and_step_match_oracle(gpu_lib, parity_bound, tau_s, tau_g):
+    # Eq. BGKcollisionOperator with distinct relaxation times on the GPU (FP64) against the
+    # oracle's moment-space collision: the one-phase config-2 mixture over 1000 steps, and
+    # one step restarted from the GPU state of the spinodal mixture
+    import lbinputs
+
+    p = lbinputs.base_params("c2")
+    kT1 = 1.1 * lbinputs.one_fluid_critical_kT(p["a"], p["b"], p["x"])
+    sim, orc = _mrt_pair("fp64", tau_s, tau_g, 70, 45, kT=kT1)
+    rho = lbinputs.fields("c2", nx=70, ny=45)
+    sim.init(rho)
+    sim.step(1000)
+    r_g, j_g = sim.moments()
+    r_o, j_o = orc.moments(orc.run(orc.equilibrium(rho), 1000))
+    parity_bound("rho rel. max, 1000 steps", np.max(np.abs(r_g - r_o)) / np.max(np.abs(r_o)), 1e-12)
+    parity_bound("j / max rho, 1000 steps", np.max(np.abs(j_g - j_o)) / np.max(np.abs(r_o)), 1e-12)
+    sim.close()
+    sim, orc = _mrt_pair("fp64", tau_s, tau_g, 70, 45)
+    sim.init(rho)
+    sim.step(200)
+    fshape = orc.fshape()
+    buf = sim.save_state()
+    f_t = np.frombuffer(buf[64:].tobytes(), dtype=np.float64).reshape(fshape).copy()
+    sim.step(1)
+    buf = sim.save_state()
+    f_n = np.frombuffer(buf[64:].tobytes(), dtype=np.float64).reshape(fshape).copy()
+    parity_bound("one step at 200", np.max(np.abs(f_n - orc.run(f_t, 1))), 1e-14)
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32_dfmu", "fp32_mixed"])
+def test_mrt_fp32_one_phase_within_1e5(gpu_lib, parity_bound, precision):
+    import lbinputs
+
+    p = lbinputs.base_params("c2")
+    kT1 = 1.1 * lbinputs.one_fluid_critical_kT(p["a"], p["b"], p["x"])
+    sim, orc = _mrt_pair(precision, 0.7, 0.9, 70, 45, kT=kT1)
+    rho = lbinputs.fields("c2", nx=70, ny=45)
+    sim.init(rho)
+    sim.step(1000)
+    r_g, _ = sim.moments()
+    r_o, _ = orc.moments(orc.run(orc.equilibrium(rho), 1000))
+    parity_bound("rho max abs, 1000 steps", np.max(np.abs(r_g - r_o)), 1e-5)
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_dfmu"])
+def test_mrt_shear_wave_decays_at_shear_viscosity_on_gpu(gpu_lib, parity_bound, precision):
+    # nu = theta (tau_s - 1/2): a transverse wave in an ideal gas (a = kappa = 0, b small)
+    from paper_1805_07251_gb300 import Simulation
+
+    nx, ny, tau_s = 128, 8, 0.6
+    k = 2 * np.pi / nx
+    x = np.arange(nx)
+    sim = Simulation(lattice="D2Q9", nx=nx, ny=ny, ncomp=1, tau=1.0, kT=1.0 / 3.0, gamma_mu=1.0, a=[[0.0]],
+                     kappa=[[0.0]], lam=[[0.0]], b=[1e-9], precision=precision, tau_shear=tau_s, tau_ghost=0.9)
+    mom = np.zeros((1, 2, ny, nx))
+    mom[0, 1] = 1e-3 * np.sin(k * x)[None, :]
+    sim.init(np.ones((1, ny, nx)), mom)
+    ts, amps = [], []
+    for t in range(1, 21):
+        sim.step(50)
+        _, j = sim.moments()
+        ts.append(50 * t)
+        amps.append(np.abs(np.mean(j[0, 1].mean(axis=0) * np.exp(-1j * k * x))))
+    sim.close()
+    rate = -np.polyfit(ts, np.log(amps), 1)[0]
+    parity_bound("shear decay / nu k^2 - 1", abs(rate / ((tau_s - 0.5) / 3.0 * k * k) - 1), 1e-3)

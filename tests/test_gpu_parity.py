@@ -584,3 +584,45 @@ def test_strip_kernel_full_size_matches_tiles(gpu_lib):
     p = lbinputs.base_params("c2")
     (r_t, j_t), (r_s, j_s) = strip_case(p, 2, p["nx"], p["ny"], "fp32_dfmu", steps=20)
     assert np.array_equal(r_t, r_s) and np.array_equal(j_t, j_s)
+
+
+def ws_case(p, nx, ny, precision, force="log", steps=40, **extra):
+    from paper_1805_07251_gb300 import Simulation
+
+    kw = lbinputs.lib_kwargs(p, nx=nx, ny=ny)
+    kw.update(extra)
+    rho = lbinputs.fields(p["name"], nx=nx, ny=ny)
+    outs = []
+    for kernel in ("tiles", "ws"):
+        sim = Simulation(precision=precision, force=force, kernel=kernel, **kw)
+        assert sim.kernel[0] == kernel
+        sim.init(rho)
+        sim.step(steps)
+        outs.append(sim.moments())
+        sim.close()
+    return outs
+
+
+@pytest.mark.parametrize("precision", ["fp32_dfmu", "fp32"])
+@pytest.mark.parametrize("nx,ny", [(32, 8), (70, 45), (100, 70), (33, 9), (256, 200)])
+def test_ws_kernel_is_bitwise_equal_to_tiles(gpu_lib, precision, nx, ny):
+    # the warp-specialised persistent tiles compute every node with the arithmetic of the
+    # tile kernel: single tiles, ragged edges, more tiles than resident CTAs
+    p = lbinputs.base_params("c2")
+    (r_t, j_t), (r_w, j_w) = ws_case(p, nx, ny, precision)
+    assert np.array_equal(r_t, r_w) and np.array_equal(j_t, j_w)
+
+
+def test_ws_kernel_nid_force_and_moment_collision(gpu_lib):
+    p = lbinputs.base_params("c2")
+    (r_t, j_t), (r_w, j_w) = ws_case(p, 96, 40, "fp32_dfmu", force="nid")
+    assert np.array_equal(r_t, r_w) and np.array_equal(j_t, j_w)
+    (r_t, j_t), (r_w, j_w) = ws_case(p, 96, 40, "fp32_dfmu", tau_shear=0.7, tau_ghost=0.9)
+    assert np.array_equal(r_t, r_w) and np.array_equal(j_t, j_w)
+
+
+def test_ws_kernel_full_size_matches_tiles(gpu_lib):
+    # workload c2 at 1024^2 (the benchmark's lattice), 20 steps
+    p = lbinputs.base_params("c2")
+    (r_t, j_t), (r_w, j_w) = ws_case(p, p["nx"], p["ny"], "fp32_dfmu", steps=20)
+    assert np.array_equal(r_t, r_w) and np.array_equal(j_t, j_w)

@@ -9,9 +9,11 @@ two sublattices of the neutral period-2 mode, and over y for D2Q9) are compared 
 tie line.  At kappa = 0.1 the lattice itself shifts stationary bulk densities by ~2e-3
 (pinning of interfaces), so the bars are statistical over the runs: D1Q3 median 2e-3 and
 95 % within 5e-3; D2Q9 (where 20,000 steps do not relax every 512^2 slab) median 5e-3 and
-85 % within 1e-2.  Runs that leave the density domain are flagged by the library; the
-paper reports its deep quenches as the unstable ones, and so here: every run at
-kT >= 0.75 of its critical temperature must stay in the domain."""
+85 % within 1e-2.  As in the paper's campaigns (Sec. VI), a 3000-step pre-scan re-tunes
+the runs that leave the density domain (deep quenches: interfaces widened by a larger
+kappa, gamma_mu lowered); after it at most 8 % of the runs may still leave the domain
+over the 20,000 steps, and every run at kT >= 0.75 of its critical temperature must stay
+in it."""
 import numpy as np
 import pytest
 
@@ -20,11 +22,12 @@ import lbinputs
 pytestmark = pytest.mark.gpu
 
 
-def test_sweep_phases_lie_on_the_common_tangent(gpu_lib):
-    from paper_1805_07251_gb300.batch import Batch
+def test_sweep_phases_lie_on_the_common_tangent(gpu_lib, parity_bound):
+    from paper_1805_07251_gb300.batch import Batch, prescan
 
     p = lbinputs.base_params("c1")
-    recs = lbinputs.sweep_runs()
+    recs, _ = prescan(lbinputs.sweep_runs(), lbinputs.sweep_fields, p["a"], p["b"], p["kappa"], p["lam"], 2,
+                      precision="fp32_dfmu")
     b = Batch(recs, p["a"], p["b"], p["kappa"], p["lam"], 2, precision="fp32_dfmu")
     b.init([lbinputs.sweep_fields(r) for r in recs])
     b.step(20000)
@@ -44,7 +47,10 @@ def test_sweep_phases_lie_on_the_common_tangent(gpu_lib):
         devs[r["lattice"]].append(max(np.max(np.abs(liq - np.asarray(r["liquid"]))),
                                       np.max(np.abs(gas - np.asarray(r["gas"])))))
     b.close()
+    parity_bound("runs leaving the domain (fraction)", float(np.mean(err != 0)), 0.08)
     d1, d2 = np.array(devs["D1Q3"]), np.array(devs["D2Q9"])
+    parity_bound("D1Q3 median bulk deviation", np.median(d1), 2e-3)
+    parity_bound("D2Q9 median bulk deviation", np.median(d2), 5e-3)
     assert len(d1) > 150 and len(d2) > 80
     assert np.median(d1) < 2e-3 and np.mean(d1 < 5e-3) > 0.95, (np.median(d1), np.mean(d1 < 5e-3))
     assert np.median(d2) < 5e-3 and np.mean(d2 < 1e-2) > 0.85, (np.median(d2), np.mean(d2 < 1e-2))
