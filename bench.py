@@ -74,8 +74,7 @@ def parse(argv=None):
 # step kernel, from an ncu capture of this script (the profile file named beside it).  The
 # value holds for the kernel sources whose digest is recorded with it and is reported as
 # null once they change.
-KERNEL_SOURCES = ("lb_kernels.cuh", "lb_lane.cuh", "lb_mu.cuh", "lb_tu.cuh", "lb_launch.cuh", "lb_d2q9_df.cu",
-                  "lb_ws.cuh")
+KERNEL_SOURCES = ("lb_kernels.cuh", "lb_lane.cuh", "lb_mu.cuh", "lb_tu.cuh", "lb_launch.cuh", "lb_d2q9_df.cu")
 TRAFFIC = {"fp32_dfmu": {"digest": "255b9ab2346c543830fd3b767b93eca8c1f2a067b99c7efcd7c78041ca35bec0",
                          "bytes": 107393280, "warp_instructions": 28700672, "issue_active": 0.577,
                          "fma_pipe_active": 0.509,

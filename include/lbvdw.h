@@ -160,7 +160,8 @@ typedef struct lb_ctx lb_ctx;
  * b before lb_create). */
 void lb_default_params(lb_params *p);
 
-/* Validate *p (symmetry of a, kappa, lambda; b > 0; tau > 1/2; sizes) and create a
+/* Validate *p (symmetry of a, kappa, lambda; b > 0; tau > 1/2; sizes: nx ny <= 2^31, and
+ * Q nx ny < 2^32 for the FP32 storage precisions) and create a
  * context on p->device: allocates two population buffers, a moments buffer and a
  * diagnostics scratch area with cudaMalloc.  No kernel runs.  On success *out owns
  * those buffers.  Errors: LB_E_INVALID, LB_E_NOMEM, LB_E_CUDA. */

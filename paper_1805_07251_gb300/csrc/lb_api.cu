@@ -306,6 +306,9 @@ lb_status lb_create(const lb_params *p, lb_ctx **out) {
     if (p->nx < 2) return LB_E_INVALID;
     if (p->lattice == LB_D1Q3 ? p->ny != 1 : p->ny < 2) return LB_E_INVALID;
     if ((int64_t)p->nx * p->ny > (int64_t)1 << 31) return LB_E_INVALID;
+    // FP32 storage: the lane-pair kernels address a component's Q planes with 32-bit offsets
+    if (p->precision != LB_FP64 && (int64_t)(p->lattice == LB_D1Q3 ? 3 : 9) * p->nx * p->ny >= (int64_t)1 << 32)
+        return LB_E_INVALID;
     if (!(p->tau > 0.5) || !(p->kT > 0.0) || !(p->gamma_mu > 0.0) || !std::isfinite(p->tau) ||
         !std::isfinite(p->kT) || !std::isfinite(p->gamma_mu))
         return LB_E_INVALID;

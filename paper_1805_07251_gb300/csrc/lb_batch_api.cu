@@ -229,7 +229,7 @@ lb_status lb_batch_create(const lb_params *shared, const lb_run_desc *runs, int3
     for (int r = 0; r < nruns; ++r) {
         const lb_run_desc &d = runs[r];
         bool ok = (d.lattice == LB_D1Q3 && d.ny == 1 && d.nx >= 2 && d.nx <= RESIDENT_MAX_L) ||
-                  (d.lattice == LB_D2Q9 && d.nx >= 2 && d.ny >= 2);
+                  (d.lattice == LB_D2Q9 && d.nx >= 2 && d.ny >= 2 && (int64_t)9 * d.nx * d.ny < ((int64_t)1 << 32));
         ok = ok && d.kT > 0.0 && d.gamma_mu > 0.0 && std::isfinite(d.kT) && std::isfinite(d.gamma_mu) &&
              d.kappa_scale >= 0.0 && std::isfinite(d.kappa_scale);
         if (!ok) {

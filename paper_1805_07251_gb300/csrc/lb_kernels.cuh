@@ -940,19 +940,22 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
 #pragma unroll
     for (int q = 0; q < NP; ++q) rref[q] = make_float2(P.rho_ref_f[2 * q], P.rho_ref_f[2 * q + 1]);
 
+    // 32-bit element offsets within a component's Q planes (Q nx ny < 2^32 for FP32
+    // storage, checked when the context is created), from per-component base pointers
+    const unsigned pl = (unsigned)plane;
     // ---- phase 1a: own node -> shared (populations, densities) ------------------
     float2 jx[NP], jy[NP];
     {
         const int gx = small ? wrap(x, nx) : wrap1(x, nx);
         const int gy = LAT == 1 ? 0 : (small ? wrap(y, ny) : wrap1(y, ny));
-        const float *src = fin + (size_t)gy * nx + gx;
+        const unsigned off = (unsigned)gy * (unsigned)nx + (unsigned)gx;
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-            const float *sq = src + 2 * q * cq;
+            const float *b0 = fin + 2 * q * cq, *b1 = b0 + cq;
             float2 gv[Q], acc;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                gv[i] = make_float2(sq[(size_t)i * plane], sq[cq + (size_t)i * plane]);
+                gv[i] = make_float2(b0[i * pl + off], b1[i * pl + off]);
                 if constexpr (STAGE) s_g[i][tid] = gv[i];
                 else if constexpr (!RELOAD) gk[q][i] = gv[i];
             }
@@ -966,13 +969,13 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
         G::ring_node(k, ex, ey);
         const int gx = small ? wrap(x0 + ex - 2, nx) : wrap1(x0 + ex - 2, nx);
         const int gy = (LAT == 1) ? 0 : (small ? wrap(y0 + ey - 2, ny) : wrap1(y0 + ey - 2, ny));
-        const float *src = fin + (size_t)gy * nx + gx;
+        const unsigned off = (unsigned)gy * (unsigned)nx + (unsigned)gx;
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-            const float *sq = src + 2 * q * cq;
-            float2 acc = make_float2(sq[0], sq[cq]);
+            const float *b0 = fin + 2 * q * cq, *b1 = b0 + cq;
+            float2 acc = make_float2(b0[off], b1[off]);
 #pragma unroll
-            for (int i = 1; i < Q; ++i) acc = v_add(acc, make_float2(sq[(size_t)i * plane], sq[cq + (size_t)i * plane]));
+            for (int i = 1; i < Q; ++i) acc = v_add(acc, make_float2(b0[i * pl + off], b1[i * pl + off]));
             s_rho[q][ey * EX + ex] = v_add(rref[q], acc);
         }
     }
@@ -1086,11 +1089,12 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
         const int cx = L::vx(i), cy = L::vy(i);
         const int dx = cx == 1 ? xe : (cx == -1 ? xw : x);
         const int dy = cy == 1 ? yn : (cy == -1 ? ys : y);
-        float *dst = fout + (size_t)i * plane + (size_t)dy * nx + dx;
+        const unsigned o = i * pl + (unsigned)dy * (unsigned)nx + (unsigned)dx;
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-            dst[2 * q * cq] = post[q][i].x;
-            dst[(2 * q + 1) * cq] = post[q][i].y;
+            float *b0 = fout + 2 * q * cq;
+            b0[o] = post[q][i].x;
+            (b0 + cq)[o] = post[q][i].y;
         }
     }
 }
