@@ -75,11 +75,11 @@ def parse(argv=None):
 # value holds for the kernel sources whose digest is recorded with it and is reported as
 # null once they change.
 KERNEL_SOURCES = ("lb_kernels.cuh", "lb_lane.cuh", "lb_mu.cuh", "lb_tu.cuh", "lb_launch.cuh", "lb_d2q9_df.cu")
-TRAFFIC = {"fp32_dfmu": {"digest": "255b9ab2346c543830fd3b767b93eca8c1f2a067b99c7efcd7c78041ca35bec0",
-                         "bytes": 107393280, "warp_instructions": 28700672, "issue_active": 0.577,
-                         "fma_pipe_active": 0.509,
-                         "stalls_per_issue": {"barrier": 3.11, "not_selected": 2.52, "long_scoreboard": 2.50,
-                                              "math_pipe_throttle": 2.14, "mio_throttle": 1.19},
+TRAFFIC = {"fp32_dfmu": {"digest": "d4b50eb8b665cb13b21cafc3925a8ee60bb0d9391782a3915b0f055381365741",
+                         "bytes": 108558080, "warp_instructions": 26959872, "issue_active": 0.554,
+                         "fma_pipe_active": 0.535,
+                         "stalls_per_issue": {"barrier": 3.04, "long_scoreboard": 2.59, "not_selected": 2.59,
+                                              "math_pipe_throttle": 2.38, "mio_throttle": 1.24},
                          "profile": "profiles/lb_step_kernel_fp32_dfmu_c2_1024.md"}}
 # instruction issue peak of the GPU: 152 SMs x 4 schedulers x 2.07 GHz (one warp instruction
 # per scheduler per cycle)
@@ -461,7 +461,8 @@ def time_adjoint(torch, dev, steps_override=0, fd=True):
     from paper_1805_07251_gb300 import Simulation, capi
 
     p = lbinputs.base_params("c5")
-    n, steps, ckpt = p["nx"], (steps_override or p["steps"]), 100
+    n, steps = p["nx"], (steps_override or p["steps"])
+    ckpt = min(100, steps)
     rho0 = lbinputs.fields("c5")
     st = torch.cuda.current_stream(dev).cuda_stream
 

@@ -93,6 +93,30 @@ cudaError_t moments(lb_ctx *c, const void *f, double *rho, double *mom) {
     return d1 ? d1q3_f32_moments(a) : d2q9_f32_moments(a);
 }
 
+// FP32 adjoint: the state's moments in FP32 (and FP64 copies) for the adjoint kernels
+template <class T>
+cudaError_t moments32(lb_ctx *c, const void *f, AdjArrays<T> A, int nb) {
+    if constexpr (sizeof(T) != 4) {
+        return cudaErrorInvalidValue;
+    } else {
+        const float *g = static_cast<const float *>(f);
+        const bool d1 = c->p.lattice == LB_D1Q3;
+        cudaStream_t st = c->stream;
+        switch (c->p.ncomp) {
+            case 1: d1 ? adj_moments32_kernel<1, 1><<<nb, ADJ_THREADS, 0, st>>>(g, A, c->dp)
+                       : adj_moments32_kernel<2, 1><<<nb, ADJ_THREADS, 0, st>>>(g, A, c->dp); break;
+            case 2: d1 ? adj_moments32_kernel<1, 2><<<nb, ADJ_THREADS, 0, st>>>(g, A, c->dp)
+                       : adj_moments32_kernel<2, 2><<<nb, ADJ_THREADS, 0, st>>>(g, A, c->dp); break;
+            case 3: d1 ? adj_moments32_kernel<1, 3><<<nb, ADJ_THREADS, 0, st>>>(g, A, c->dp)
+                       : adj_moments32_kernel<2, 3><<<nb, ADJ_THREADS, 0, st>>>(g, A, c->dp); break;
+            case 4: d1 ? adj_moments32_kernel<1, 4><<<nb, ADJ_THREADS, 0, st>>>(g, A, c->dp)
+                       : adj_moments32_kernel<2, 4><<<nb, ADJ_THREADS, 0, st>>>(g, A, c->dp); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
+}
+
 template <class T>
 lb_status backward(lb_ctx *c, const double *rho_bar_T, double *rho_bar_0, double *grad) {
     const int N = c->p.ncomp, Q = c->Q, D = c->D;
@@ -119,6 +143,12 @@ lb_status backward(lb_ctx *c, const double *rho_bar_T, double *rho_bar_0, double
     A.lapb = mem.get<T>((size_t)N * n);
     A.mub = mem.get<T>((size_t)N * n);
     A.partial = mem.get<double>((size_t)(nb + 1) * V);
+    A.rho_t = A.u_t = nullptr;
+    if (sizeof(T) == 4) {
+        A.rho_t = mem.get<float>((size_t)N * n);
+        A.u_t = mem.get<float>((size_t)N * D * n);
+        if (!A.rho_t || !A.u_t) return rfail(c, LB_E_NOMEM, "adjoint work allocation");
+    }
     double *accum = mem.get<double>(V);
     double *rb0 = mem.get<double>((size_t)N * n);
     if (!fb[0] || !fb[1] || !rho || !jj || !A.lap || !A.phi || !A.rhob || !A.jb || !A.dphib || !A.drhob ||
@@ -141,7 +171,9 @@ lb_status backward(lb_ctx *c, const double *rho_bar_T, double *rho_bar_0, double
         for (int m = 1; m < len; ++m)
             if (lb_ctx_step(c, ring[m - 1], ring[m]) != cudaSuccess) return rfail(c, LB_E_CUDA, "recompute step");
         for (int m = len - 1; m >= 0; --m) {
-            if (moments(c, ring[m], rho, jj) != cudaSuccess) return rfail(c, LB_E_CUDA, "moments");
+            const cudaError_t em = sizeof(T) == 4 ? moments32(c, ring[m], A, nb)
+                                                   : moments(c, ring[m], rho, jj);
+            if (em != cudaSuccess) return rfail(c, LB_E_CUDA, "moments");
             cudaError_t e = d1 ? adjoint_step_n<1, T>(N, fb[cur], fb[cur ^ 1], A, c->dp, nb, accum, st)
                                : adjoint_step_n<2, T>(N, fb[cur], fb[cur ^ 1], A, c->dp, nb, accum, st);
             if (e != cudaSuccess) return rfail(c, LB_E_CUDA, "adjoint step");

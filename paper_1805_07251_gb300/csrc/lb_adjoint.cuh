@@ -4,8 +4,12 @@
 // The kernels are templates over T, the type of the adjoint populations and of their
 // arithmetic: double for the FP64 rollout, float for the FP32 rollouts.  In both, the
 // forward recompute of the chemical potential (phi = gamma mu, its gradient) and the
-// transpose of its Jacobian d mu / d rho run in FP64, the moments of the forward state
-// arrive in FP64, and the parameter-gradient partials are summed in FP64.
+// transpose of its Jacobian d mu / d rho run in FP64, and the parameter gradients are
+// summed in FP64 across CTAs.  The FP32 rollouts take the moments of the stored state as
+// the FP32 step forms them (rho = rho_ref + sum_i g_i in FP32, adj_moments32_kernel),
+// widened to FP64 for mu, and keep everything outside mu on the FP32 pipe (rho, u and
+// D rho in FP32, reciprocals from an FP32 seed refined in FP64, per-CTA partial sums in
+// FP32).
 //
 // Forward step (per node x, component c; D = central difference, Lap = lattice
 // Laplacian, theta = 1/3):
@@ -40,7 +44,50 @@ struct AdjArrays {
     double *phi;                 // [N][n], gamma mu in FP64
     T *rhob, *jb, *dphib, *drhob, *lapb, *mub;  // adjoint intermediates
     double *partial;             // [blocks][2 N^2 + N] parameter-gradient partials
+    // FP32 adjoint only: rho and u = j / rho of the state in FP32, written by adj_mu_kernel,
+    // so that the parts of the local transpose outside mu stay off the FP64 pipe
+    float *rho_t, *u_t;          // [N][n], [N][D][n]
 };
+
+template <class T> struct IsF32 { static constexpr bool value = false; };
+template <> struct IsF32<float> { static constexpr bool value = true; };
+
+// 1 / x in FP64 from an FP32 seed and two Newton steps (y <- y + y (1 - x y)), within an
+// ulp or two of the quotient for the positive, normal x of this code (densities, eta)
+__device__ __forceinline__ double recip64(double x) {
+    double y = (double)__frcp_rn((float)x);
+    y = fma(y, fma(-x, y, 1.0), y);
+    return fma(y, fma(-x, y, 1.0), y);
+}
+
+// Block sum of V per-thread values into one FP64 partial per CTA (fixed order): in FP64
+// for the FP64 adjoint, for the FP32 adjoint warp shuffles in FP32 and the warp sums in
+// FP64
+template <class T, int V>
+__device__ __forceinline__ void block_sum_adj(T (&v)[V], double *out) {
+    if constexpr (!IsF32<T>::value) {
+        block_sum<V>(v, out);
+    } else {
+        __shared__ double s_part[ADJ_THREADS / 32][V];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < V; ++k) s_part[wid][k] = (double)v[k];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                double acc = 0.0;
+                for (int w = 0; w < ADJ_THREADS / 32; ++w) acc += s_part[w][k];
+                out[k] = acc;
+            }
+        }
+    }
+}
 
 template <int LAT>
 struct Nb {
@@ -104,6 +151,42 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_mu_kernel(AdjArrays<T> A, Dev
     }
 }
 
+// Moments of an FP32-storage state for the FP32 adjoint: rho^c = rho_ref^c + sum_i g_i and
+// the bare momenta summed in FP32 in direction order, as the forward step kernel forms them,
+// then u = j / rho in FP32; rho and j also in FP64 for the FP64 chemical potential.
+template <int LAT, int N>
+__global__ void __launch_bounds__(ADJ_THREADS) adj_moments32_kernel(const float *__restrict__ g, AdjArrays<float> A,
+                                                                    DevParams P) {
+    using L = Lat<LAT>;
+    constexpr int Q = L::Q, D = L::D;
+    const size_t n = (size_t)P.nx * P.ny;
+    const size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    double *rho = const_cast<double *>(A.rho), *j = const_cast<double *>(A.j);
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        float v[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) v[i] = g[(size_t)(c * Q + i) * n + s];
+        float acc = v[0], jx = 0.0f, jy = 0.0f;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            acc += v[i];
+            if (L::vx(i) != 0) jx += L::vx(i) == 1 ? v[i] : -v[i];
+            if (L::vy(i) != 0) jy += L::vy(i) == 1 ? v[i] : -v[i];
+        }
+        const float r = P.rho_ref_f[c] + acc;
+        A.rho_t[c * n + s] = r;
+        rho[c * n + s] = (double)r;
+        A.u_t[(c * D) * n + s] = jx / r;
+        j[(c * D) * n + s] = (double)jx;
+        if (D == 2) {
+            A.u_t[(c * D + 1) * n + s] = jy / r;
+            j[(c * D + 1) * n + s] = (double)jy;
+        }
+    }
+}
+
 // ---- local transpose of collision, forcing, Psi, friction, force -------------------------
 template <int LAT, int N, class T>
 __global__ void __launch_bounds__(ADJ_THREADS)
@@ -122,13 +205,21 @@ __global__ void __launch_bounds__(ADJ_THREADS)
     T W[N][N], M[N][N];
 #pragma unroll
     for (int c = 0; c < N; ++c) {
-        rho[c] = T(A.rho[c * n + s]);
-        double px, py, qx, qy;
-        grad_g<LAT>(A.phi + c * n, x, y, nx, ny, px, py);
-        grad_g<LAT>(A.rho + c * n, x, y, nx, ny, qx, qy);
-        dphi[c][0] = T(px), dphi[c][1] = T(py), drho[c][0] = T(qx), drho[c][1] = T(qy);
+        double px, py;
+        grad_g<LAT>(A.phi + c * n, x, y, nx, ny, px, py);  // D phi in FP64 (FP64 mu)
+        dphi[c][0] = T(px), dphi[c][1] = T(py);
+        if constexpr (IsF32<T>::value) {
+            rho[c] = A.rho_t[c * n + s];
+            grad_g<LAT>(A.rho_t + c * n, x, y, nx, ny, drho[c][0], drho[c][1]);
+            for (int a = 0; a < 2; ++a) u[c][a] = (a < D) ? A.u_t[(c * D + a) * n + s] : T(0);
+        } else {
+            rho[c] = T(A.rho[c * n + s]);
+            double qx, qy;
+            grad_g<LAT>(A.rho + c * n, x, y, nx, ny, qx, qy);
+            drho[c][0] = T(qx), drho[c][1] = T(qy);
+            for (int a = 0; a < 2; ++a) u[c][a] = (a < D) ? T(A.j[(c * D + a) * n + s] / A.rho[c * n + s]) : T(0);
+        }
         for (int a = 0; a < 2; ++a) {
-            u[c][a] = (a < D) ? T(A.j[(c * D + a) * n + s] / A.rho[c * n + s]) : T(0);
             gmu[c][a] = (a < D) ? -rho[c] * dphi[c][a] + th * drho[c][a] : T(0);
             G[c][a] = gmu[c][a];
         }
@@ -324,9 +415,12 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_mubar_kernel(AdjArrays<T> A, 
     const int nx = P.nx, ny = P.ny;
     const size_t n = (size_t)nx * ny;
     const size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    double acc[V];
+    double acc[IsF32<T>::value ? 1 : V];
+    float acc32[IsF32<T>::value ? V : 1];
 #pragma unroll
-    for (int k = 0; k < V; ++k) acc[k] = 0.0;
+    for (int k = 0; k < (IsF32<T>::value ? 1 : V); ++k) acc[k] = 0.0;
+#pragma unroll
+    for (int k = 0; k < (IsF32<T>::value ? V : 1); ++k) acc32[k] = 0.0f;
     if (s < n) {
         const int x = (int)(s % nx), y = (int)(s / nx);
         double mb[N], r[N], eta = 1.0, rt = 0.0;
@@ -350,17 +444,34 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_mubar_kernel(AdjArrays<T> A, 
         }
         // d mu^c / d a_cd = -2 rho^d;  d mu^c / d kappa_cd = -Lap rho^d;
         // d mu^c / d b^d = kT [rho^d/eta + delta_cd rho_t/eta + b^c rho_t rho^d / eta^2]
+        if constexpr (!IsF32<T>::value) {
 #pragma unroll
-        for (int c = 0; c < N; ++c)
+            for (int c = 0; c < N; ++c)
 #pragma unroll
-            for (int d = 0; d < N; ++d) {
-                acc[c * N + d] = mb[c] * (-2.0 * r[d]);
-                acc[N * N + c * N + d] = mb[c] * (-(double)A.lap[d * n + s]);
-                acc[2 * N * N + d] += mb[c] * P.kT *
-                                      (r[d] / eta + (c == d ? rt / eta : 0.0) + P.b[c] * rt * r[d] / (eta * eta));
-            }
+                for (int d = 0; d < N; ++d) {
+                    acc[c * N + d] = mb[c] * (-2.0 * r[d]);
+                    acc[N * N + c * N + d] = mb[c] * (-(double)A.lap[d * n + s]);
+                    acc[2 * N * N + d] += mb[c] * P.kT *
+                                          (r[d] / eta + (c == d ? rt / eta : 0.0) + P.b[c] * rt * r[d] / (eta * eta));
+                }
+        } else {
+            // the FP32 adjoint: the a and kappa terms in FP32, the b term (the Jacobian of
+            // mu's FP64 part) in FP64 with one reciprocal of eta
+            const double ieta = recip64(eta);
+#pragma unroll
+            for (int c = 0; c < N; ++c)
+#pragma unroll
+                for (int d = 0; d < N; ++d) {
+                    acc32[c * N + d] = (float)mb[c] * (-2.0f * A.rho_t[d * n + s]);
+                    acc32[N * N + c * N + d] = (float)mb[c] * (-(float)A.lap[d * n + s]);
+                    acc32[2 * N * N + d] += (float)(mb[c] * P.kT *
+                                                    (r[d] * ieta + (c == d ? rt * ieta : 0.0) +
+                                                     P.b[c] * rt * r[d] * ieta * ieta));
+                }
+        }
     }
-    block_sum<V>(acc, A.partial + (size_t)blockIdx.x * V);
+    if constexpr (!IsF32<T>::value) block_sum_adj<double, V>(acc, A.partial + (size_t)blockIdx.x * V);
+    else block_sum_adj<float, V>(acc32, A.partial + (size_t)blockIdx.x * V);
 }
 
 // ---- rhobar and fbar ---------------------------------------------------------------------
@@ -381,14 +492,17 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_rhobar_kernel(T *__restrict__
         eta -= P.b[c] * r[c];
         rt += r[c];
     }
-    const double ieta = 1.0 / eta;
+    // reciprocals: FP64 quotients for the FP64 adjoint; for the FP32 adjoint an FP32 seed
+    // refined in FP64 (recip64), which keeps the divisions off the FP64 pipe's slow path
+    const double ieta = IsF32<T>::value ? recip64(eta) : 1.0 / eta;
 #pragma unroll
     for (int d = 0; d < N; ++d) {
         // local chemical-potential Jacobian (kT part and the -2a term), in FP64
         double jt = 0.0;
 #pragma unroll
         for (int c = 0; c < N; ++c) {
-            double J = P.kT * ((c == d ? 1.0 / r[c] : 0.0) + (P.b[c] + P.b[d]) * ieta + P.b[c] * P.b[d] * rt * ieta * ieta) -
+            const double ir = c == d ? (IsF32<T>::value ? recip64(r[c]) : 1.0 / r[c]) : 0.0;
+            double J = P.kT * (ir + (P.b[c] + P.b[d]) * ieta + P.b[c] * P.b[d] * rt * ieta * ieta) -
                        2.0 * P.a[c * 4 + d];
             jt += mb[c] * J;
         }
