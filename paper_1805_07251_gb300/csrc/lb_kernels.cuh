@@ -940,9 +940,16 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
 #pragma unroll
     for (int q = 0; q < NP; ++q) rref[q] = make_float2(P.rho_ref_f[2 * q], P.rho_ref_f[2 * q + 1]);
 
-    // 32-bit element offsets within a component's Q planes (Q nx ny < 2^32 for FP32
-    // storage, checked when the context is created), from per-component base pointers
+    // One pair: 32-bit element offsets within a component's Q planes (Q nx ny < 2^32 for
+    // FP32 storage, checked when the context is created) from per-component base pointers,
+    // which saves address arithmetic; two pairs keep 64-bit addressing (the extra base
+    // pointers would spill at their 64 registers).
     const unsigned pl = (unsigned)plane;
+    // element e of plane i of component c, from the node offset o of plane 0
+    auto ld = [&](int c, int i, unsigned o) -> float {
+        if constexpr (NP == 1) return (fin + c * cq)[i * pl + o];
+        else return fin[(size_t)c * cq + (size_t)i * plane + o];
+    };
     // ---- phase 1a: own node -> shared (populations, densities) ------------------
     float2 jx[NP], jy[NP];
     {
@@ -951,11 +958,10 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
         const unsigned off = (unsigned)gy * (unsigned)nx + (unsigned)gx;
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-            const float *b0 = fin + 2 * q * cq, *b1 = b0 + cq;
             float2 gv[Q], acc;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                gv[i] = make_float2(b0[i * pl + off], b1[i * pl + off]);
+                gv[i] = make_float2(ld(2 * q, i, off), ld(2 * q + 1, i, off));
                 if constexpr (STAGE) s_g[i][tid] = gv[i];
                 else if constexpr (!RELOAD) gk[q][i] = gv[i];
             }
@@ -972,10 +978,9 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
         const unsigned off = (unsigned)gy * (unsigned)nx + (unsigned)gx;
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-            const float *b0 = fin + 2 * q * cq, *b1 = b0 + cq;
-            float2 acc = make_float2(b0[off], b1[off]);
+            float2 acc = make_float2(ld(2 * q, 0, off), ld(2 * q + 1, 0, off));
 #pragma unroll
-            for (int i = 1; i < Q; ++i) acc = v_add(acc, make_float2(b0[i * pl + off], b1[i * pl + off]));
+            for (int i = 1; i < Q; ++i) acc = v_add(acc, make_float2(ld(2 * q, i, off), ld(2 * q + 1, i, off)));
             s_rho[q][ey * EX + ex] = v_add(rref[q], acc);
         }
     }
@@ -1089,12 +1094,17 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
         const int cx = L::vx(i), cy = L::vy(i);
         const int dx = cx == 1 ? xe : (cx == -1 ? xw : x);
         const int dy = cy == 1 ? yn : (cy == -1 ? ys : y);
-        const unsigned o = i * pl + (unsigned)dy * (unsigned)nx + (unsigned)dx;
+        if constexpr (NP == 1) {
+            const unsigned o = i * pl + (unsigned)dy * (unsigned)nx + (unsigned)dx;
+            fout[o] = post[0][i].x;
+            (fout + cq)[o] = post[0][i].y;
+        } else {
+            float *dst = fout + (size_t)i * plane + (size_t)dy * nx + dx;
 #pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            float *b0 = fout + 2 * q * cq;
-            b0[o] = post[q][i].x;
-            (b0 + cq)[o] = post[q][i].y;
+            for (int q = 0; q < NP; ++q) {
+                dst[2 * q * cq] = post[q][i].x;
+                dst[(2 * q + 1) * cq] = post[q][i].y;
+            }
         }
     }
 }

@@ -148,3 +148,18 @@ def test_relaxation_times_are_validated_without_cuda(lib):
     runs = (capi.lb_run_desc * 1)()
     runs[0].lattice, runs[0].nx, runs[0].ny, runs[0].kT, runs[0].gamma_mu = capi.LB_D2Q9, 64, 64, 1.0 / 3.0, 0.1
     assert lib.lb_batch_create(ctypes.byref(p), runs, 1, ctypes.byref(out)) == capi.LB_E_INVALID
+
+
+def test_warp_specialised_kernel_is_validated_without_cuda(lib):
+    # LB_KERNEL_WS: D2Q9, two components, FP32 storage with an FP32-class mu, 32 x 8 tiles
+    from paper_1805_07251_gb300 import capi
+
+    out = ctypes.c_void_p()
+    for change in ({"ncomp": 3}, {"precision": capi.LB_FP64}, {"precision": capi.LB_FP32_MIXED},
+                   {"tile_x": 64, "tile_y": 4}, {"lattice": capi.LB_D1Q3, "ny": 1}):
+        p = capi.lb_default_params()
+        p.b[0] = p.b[1] = p.b[2] = 0.3
+        p.precision, p.kernel = capi.LB_FP32_DFMU, capi.LB_KERNEL_WS
+        for k, v in change.items():
+            setattr(p, k, v)
+        assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID, change
