@@ -75,11 +75,11 @@ def parse(argv=None):
 # value holds for the kernel sources whose digest is recorded with it and is reported as
 # null once they change.
 KERNEL_SOURCES = ("lb_kernels.cuh", "lb_lane.cuh", "lb_mu.cuh", "lb_tu.cuh", "lb_launch.cuh", "lb_d2q9_df.cu")
-TRAFFIC = {"fp32_dfmu": {"digest": "d4b50eb8b665cb13b21cafc3925a8ee60bb0d9391782a3915b0f055381365741",
-                         "bytes": 108558080, "warp_instructions": 26959872, "issue_active": 0.554,
-                         "fma_pipe_active": 0.535,
-                         "stalls_per_issue": {"barrier": 3.04, "long_scoreboard": 2.59, "not_selected": 2.59,
-                                              "math_pipe_throttle": 2.38, "mio_throttle": 1.24},
+TRAFFIC = {"fp32_dfmu": {"digest": "2137365bdf95ec855ec85c16525185470f30a20634a5c9c75b9f7f2686518a6e",
+                         "bytes": 108305920, "warp_instructions": 27213824, "issue_active": 0.558,
+                         "fma_pipe_active": 0.536,
+                         "stalls_per_issue": {"barrier": 2.94, "not_selected": 2.70, "long_scoreboard": 2.49,
+                                              "math_pipe_throttle": 2.41, "mio_throttle": 1.17},
                          "profile": "profiles/lb_step_kernel_fp32_dfmu_c2_1024.md"}}
 # instruction issue peak of the GPU: 152 SMs x 4 schedulers x 2.07 GHz (one warp instruction
 # per scheduler per cycle)
