@@ -141,10 +141,15 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_mu_kernel(AdjArrays<T> A, Dev
         eta -= P.b[c] * r[c];
         rt += r[c];
     }
-    const double ieta = 1.0 / eta;
+    // FP64 throughout; the FP32 adjoint takes the table-driven FP64 logarithm of the
+    // forward's FP64-mu path (lb_mu.cuh) and an FP32-seeded reciprocal refined in FP64
+    const double ieta = IsF32<T>::value ? recip64(eta) : 1.0 / eta;
 #pragma unroll
     for (int c = 0; c < N; ++c) {
-        double m = P.kT * (log(r[c] * ieta) + P.b[c] * rt * ieta);
+        const double lg = IsF32<T>::value ? log64_tbl(r[c] * ieta, P.tbl->r64, P.tbl->t64_hi, P.tbl->t64_lo,
+                                                      P.tbl->ln2_hi_d, P.tbl->ln2_lo_d)
+                                          : log(r[c] * ieta);
+        double m = P.kT * (lg + P.b[c] * rt * ieta);
 #pragma unroll
         for (int d = 0; d < N; ++d) m -= 2.0 * P.a[c * 4 + d] * r[d] + P.kappa[c * 4 + d] * lp[d];
         A.phi[c * n + s] = P.gamma * m;

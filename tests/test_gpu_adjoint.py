@@ -236,3 +236,48 @@ def test_fp32_gradients_against_fp64(gpu_lib, parity_bound, lattice, precision):
     parity_bound("dL/dkappa vs FP64 adjoint (rel.)", dk, 1e-3)
     parity_bound("dL/db vs FP64 adjoint (rel. max)", db, 1e-3)
     parity_bound("dL/drho0 vs FP64 adjoint (rel. max)", dr, 1e-3)
+
+
+@pytest.mark.parametrize("N,precision", [(3, "fp64"), (4, "fp64"), (4, "fp32_dfmu")])
+def test_adjoint_more_components(gpu_lib, parity_bound, N, precision):
+    # the adjoint kernels for N = 3, 4 (the forward's general N-component friction solve;
+    # for FP32 storage and four components the forward runs as two lane pairs): dL/da_12
+    # and dL/dkappa against Richardson-extrapolated central differences of the FP64 forward
+    from paper_1805_07251_gb300 import Simulation, capi
+
+    r = np.random.default_rng(300 + N)
+    a = r.uniform(0.5, 1.2, (N, N)); a = 0.5 * (a + a.T); np.fill_diagonal(a, 1.0)
+    b = r.uniform(0.2, 0.35, N)
+    x = np.full(N, 1.0 / N)
+    kT = 1.05 * lbinputs.one_fluid_critical_kT(a, b, x)
+    lam = np.ones((N, N)) - np.eye(N)
+    nx, ny, steps = 24, 20, 40
+    rho0 = lbinputs.uniform_noise_fields(N, ny, nx, 1.3 * x, 1e-2, 4000 + N)
+    tgt = rho0 + np.random.default_rng(5).normal(0, 1e-2, rho0.shape)
+
+    def make(aa, kap, prec):
+        return Simulation(lattice="D2Q9", nx=nx, ny=ny, ncomp=N, tau=1.0, kT=kT, gamma_mu=0.1, a=aa,
+                          kappa=np.full((N, N), kap), lam=lam, b=b, precision=prec)
+
+    def loss(a12, kap):
+        aa = a.copy(); aa[0, 1] = aa[1, 0] = a12
+        s = make(aa, kap, "fp64")
+        s.init(rho0)
+        s.step(steps)
+        rr, _ = s.moments()
+        s.close()
+        return float(np.sum((rr - tgt) ** 2))
+
+    s = make(a, 0.1, precision)
+    s.init(rho0)
+    capi.lb_rollout_forward(s.ctx, steps, 16)
+    rr, _ = s.moments()
+    _, g = capi.lb_rollout_backward(s.ctx, 2.0 * (rr - tgt), N)
+    s.close()
+    ga = g[1] + g[N]
+    gk = g[N * N: 2 * N * N].sum()
+    fa = central(lambda v: loss(v, 0.1), a[0, 1], 1e-4)
+    fk = central(lambda v: loss(a[0, 1], v), 0.1, 1e-4)
+    bar = 1e-6 if precision == "fp64" else 1e-3
+    parity_bound("dL/da12 vs FD (rel.)", abs(ga - fa) / abs(fa), bar)
+    parity_bound("dL/dkappa vs FD (rel.)", abs(gk - fk) / abs(fk), bar)
