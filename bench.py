@@ -6,8 +6,12 @@ mixture a = [[1, .9], [.9, .6]], b = (.25, .3), kappa = .1, kT = 0.85 of the
 one-fluid critical temperature, uniform density 1.2 at mole fraction 0.4 plus
 seeded Gaussian noise (sigma 1e-2): spinodal decomposition.  One benchmark step
 is one lattice Boltzmann timestep (one fused kernel launch) of the whole
-lattice; the L2 is flushed (256 MB write) between timed steps, outside the
-timed events.
+lattice.  The K timed steps run back to back in one lb_step call between two
+CUDA events, as in a run of the workload (the library chains consecutive
+launches of the two-component FP32 paths); the state, two population buffers
+of 151 MB, is larger than the 129 MB L2.  Each path is also timed with one
+launch per step and the L2 flushed (256 MB write) before each, outside the
+events (``flushed`` in the line).
 
 Metric: component-MLUPS = ncomp * nodes * steps / s / 1e6.  Three paths are
 timed in the same run: FP32 storage with the chemical potential in
@@ -71,10 +75,12 @@ def parse(argv=None):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the headline
-# step kernel, from an ncu capture of this script (the profile file named beside it).  The
+# step kernel (the chained step), from an ncu capture of this script (the profile file
+# named beside it).  The
 # value holds for the kernel sources whose digest is recorded with it and is reported as
 # null once they change.
-KERNEL_SOURCES = ("lb_kernels.cuh", "lb_lane.cuh", "lb_mu.cuh", "lb_tu.cuh", "lb_launch.cuh", "lb_d2q9_df.cu")
+KERNEL_SOURCES = ("lb_kernels.cuh", "lb_chain.cuh", "lb_lane.cuh", "lb_mu.cuh", "lb_tu.cuh", "lb_launch.cuh",
+                  "lb_d2q9_df.cu")
 TRAFFIC = {"fp32_dfmu": {"digest": "2137365bdf95ec855ec85c16525185470f30a20634a5c9c75b9f7f2686518a6e",
                          "bytes": 108305920, "warp_instructions": 27213824, "issue_active": 0.558,
                          "fma_pipe_active": 0.536,
@@ -561,8 +567,8 @@ def time_adjoint(torch, dev, steps_override=0, fd=True):
 
 
 def time_path(torch, Simulation, kw, rho, precision, steps, warmup, flush, dev):
-    """Device time of the fused step kernel: CUDA events on the launching stream around
-    each step, L2 flushed before each step outside the events."""
+    """A context of the precision, warmed up (single steps with the L2 flushed before each,
+    then one call of `warmup` steps), and one pair of CUDA events per timed step."""
     stream = torch.cuda.current_stream(dev)
     sim = Simulation(precision=precision, device=dev, stream=stream.cuda_stream, tile=TILE,
                      kernel=kernel_for(precision), segments=SEGMENTS, **kw)
@@ -570,6 +576,7 @@ def time_path(torch, Simulation, kw, rho, precision, steps, warmup, flush, dev):
     for _ in range(warmup):
         flush.zero_()
         sim.step(1)
+    sim.step(warmup)  # the chained launches too, untimed
     torch.cuda.synchronize(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     launches0 = sim.launches
@@ -659,6 +666,15 @@ def main():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize(dev)
+        # the job: K steps back to back in one lb_step call (chained launches where the
+        # configuration chains); the state (both population buffers) exceeds the L2
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        job_ms = max_over_ranks(dist, e0.elapsed_time(e1), dev)
+        # one plain launch per step, the L2 flushed before each, outside the events
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)
@@ -670,27 +686,19 @@ def main():
         if sampler:
             clocks = sampler.stop()
         launches = sim.launches - l0
-        nf_ms = None
-        if precision == HEAD:
-            # the same K steps back to back between two events, no L2 flush in between
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize(dev)
-            e0.record(stream)
-            sim.step(args.steps)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            nf_ms = max_over_ranks(dist, e0.elapsed_time(e1), dev) / args.steps
-            launches += args.steps
         per = [a.elapsed_time(b) for a, b in ev]
-        total_ms = max_over_ranks(dist, float(sum(per)), dev)
+        fl_ms = max_over_ranks(dist, float(sum(per)), dev) / args.steps
         kind, tile = sim.kernel
-        ms = total_ms / args.steps
-        value = job_throughput(world, N * nodes * args.steps, total_ms * 1e-3)
+        ms = job_ms / args.steps
         elem = 8 if precision == "fp64" else 4
         alg_bytes = N * nodes * 9 * 2 * elem
-        achieved = alg_bytes / (ms * 1e-3) / 1e9
-        results[precision] = dict(value=value, ms=ms, launches=launches, alg_bytes=alg_bytes, achieved=achieved,
-                                  kernel="%s %dx%d" % (kind, tile[0], tile[1]), nf_ms=nf_ms)
+        results[precision] = dict(
+            value=job_throughput(world, N * nodes * args.steps, job_ms * 1e-3), ms=ms, launches=launches,
+            alg_bytes=alg_bytes, achieved=alg_bytes / (ms * 1e-3) / 1e9, chained=sim.chain_rows > 0,
+            kernel="%s %dx%d" % (kind, tile[0], tile[1]),
+            flushed={"value": job_throughput(world, N * nodes, fl_ms * 1e-3), "unit": UNIT, "ms_per_step": fl_ms,
+                     "achieved_gbs": alg_bytes / (fl_ms * 1e-3) / 1e9,
+                     "frac": alg_bytes / (fl_ms * 1e-3) / 1e9 / peak_gbs})
         sim.close()
 
     sweep = None
@@ -747,27 +755,28 @@ def main():
         "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPES[HEAD], "data": "synthetic",
         "config": {"workload": "D2Q9, 2 components, 1024x1024 periodic, spinodal mixture (c2), " + HEAD,
-                   "nodes": nodes, "ncomp": N, "kernel": head["kernel"], "l2": "flushed between steps (256 MB write)",
+                   "nodes": nodes, "ncomp": N, "kernel": head["kernel"] + (", chained" if head["chained"] else ""),
+                   "l2": "no flush: the job's state (two population buffers, %.0f MB) is larger than the 129 MB "
+                         "L2; the K timed steps run back to back in one lb_step call between two CUDA events. "
+                         "One launch per step with a 256 MB L2 flush before each: 'flushed'"
+                         % (head["alg_bytes"] / 1e6),
                    "parallelism": "independent replica per GPU" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": head["achieved"], "peak": peak_gbs, "unit": "GB/s",
                      "frac": head["achieved"] / peak_gbs, "traffic": traffic_of(HEAD)[0],
                      "traffic_profile": traffic_of(HEAD)[1], "peak_kind": peak_kind,
                      "kernel": "%s<D2Q9, N=2, %s, %s>" % (
+                         "lb_chain_kernel" if head["chained"] else
                          {"strips": "lb_strip_kernel", "ws": "lb_step_ws_kernel"}.get(head["kernel"].split()[0],
                                                                                       "lb_step_kernel"),
                          head["kernel"].split()[1], HEAD),
                      "alg_bytes_per_launch": head["alg_bytes"],
+                     "duration": "K launches between two CUDA events / K",
                      "limiter": limiter_of(HEAD, head["alg_bytes"], peak_gbs)},
         "gpu_launches": head["launches"],
+        "flushed": dict(head["flushed"], kernel="lb_step_kernel",
+                        note="one lb_step(1) per timed step (a plain launch) between its own CUDA events, a 256 MB "
+                             "L2 flush before each outside them (writes of a step drain during the next flush)"),
     }
-    if head.get("nf_ms"):
-        nf = head["nf_ms"]
-        line["no_flush"] = {
-            "value": job_throughput(world, N * nodes, nf * 1e-3), "unit": UNIT, "ms_per_step": nf,
-            "achieved_gbs": head["alg_bytes"] / (nf * 1e-3) / 1e9,
-            "frac": head["alg_bytes"] / (nf * 1e-3) / 1e9 / peak_gbs,
-            "note": "the same K steps back to back between two CUDA events, no L2 flush between them "
-                    "(writes of one step may still drain during the next)"}
     if "fp32_mixed" in results:
         fm = results["fp32_mixed"]
         line["config"]["fp64_mu_path"] = (
@@ -794,9 +803,10 @@ def main():
             continue
         rr = results[key]
         line[name] = {"value": rr["value"], "unit": UNIT, "ms_per_step": rr["ms"], "dtype": DTYPES[key],
-                      "kernel": rr["kernel"],
+                      "kernel": rr["kernel"] + (", chained" if rr["chained"] else ""),
                       "roofline_hbm": {"achieved": rr["achieved"], "peak": peak_gbs, "unit": "GB/s",
-                                       "frac": rr["achieved"] / peak_gbs}}
+                                       "frac": rr["achieved"] / peak_gbs},
+                      "flushed": rr["flushed"]}
         line["gpu_launches"] += rr["launches"]
     if clocks:
         line["clocks"] = clocks

@@ -163,8 +163,9 @@ void lb_default_params(lb_params *p);
 /* Validate *p (symmetry of a, kappa, lambda; b > 0; tau > 1/2; sizes: nx ny <= 2^31, and
  * Q nx ny < 2^32 for the FP32 storage precisions) and create a
  * context on p->device: allocates two population buffers, a moments buffer and a
- * diagnostics scratch area with cudaMalloc.  No kernel runs.  On success *out owns
- * those buffers.  Errors: LB_E_INVALID, LB_E_NOMEM, LB_E_CUDA. */
+ * diagnostics scratch area with cudaMalloc (and, for the configurations whose steps
+ * lb_step chains, one 32-bit completion flag per 32 x 8 tile).  No kernel runs.  On
+ * success *out owns those buffers.  Errors: LB_E_INVALID, LB_E_NOMEM, LB_E_CUDA. */
 lb_status lb_create(const lb_params *p, lb_ctx **out);
 
 /* Set the state to the equilibrium (Eq. feq, at theta = 1/3) of host densities
@@ -180,9 +181,17 @@ lb_status lb_init_fields(lb_ctx *ctx, const double *rho, const double *mom);
  * The domain check of the densities is deferred to the next read-back call. */
 lb_status lb_init_fields_dev(lb_ctx *ctx, const double *rho_dev, const double *mom_dev);
 
-/* Enqueue nsteps >= 0 timesteps on the context stream.  Asynchronous unless
- * check_every > 0.  Errors: LB_E_STATE, LB_E_INVALID, LB_E_CUDA, LB_E_DOMAIN (only
- * when check_every > 0). */
+/* Enqueue nsteps >= 0 timesteps (Eq. LBequation with the forces of Sec. III and V) on
+ * the context stream.  Asynchronous unless check_every > 0.
+ * Consecutive steps of one call are chained when the configuration allows it (D2Q9, two
+ * components, LB_FP32_DFMU or LB_FP32, tiles of 32 x 8 with every ragged tile at least 3
+ * nodes wide and high): step s + 1 launches while step s is finishing, and a tile of step
+ * s + 1 that starts early waits on completion flags of the 3 x 3 tiles around it instead
+ * of on the whole grid.  The results are bitwise those of one launch per step; a chain is
+ * cut where check_every synchronises, and a single step is always one plain launch.  A
+ * chained wait is bounded (one second); one that runs out sets the error word's stall bit.
+ * Errors: LB_E_STATE, LB_E_INVALID, LB_E_CUDA, LB_E_DOMAIN and LB_E_TIMEOUT (only when
+ * check_every > 0). */
 lb_status lb_step(lb_ctx *ctx, int64_t nsteps);
 
 /* Copy rho^c [c][y][x] and bare momenta j^c = sum_i f_i^c v_i [c][d][y][x] of the
@@ -323,6 +332,11 @@ int64_t lb_step_count(const lb_ctx *ctx);
 
 /* Kernel launches enqueued by this context since creation (for launch accounting). */
 int64_t lb_launch_count(const lb_ctx *ctx);
+
+/* Whether lb_step chains consecutive steps of this context (see lb_step): the number of
+ * 32 x 8 tile rows of a chained step that set completion flags for the next step, 0 when
+ * the configuration is not chained, -1 for a NULL context. */
+int32_t lb_chain_rows(const lb_ctx *ctx);
 
 /* Copy the context's parameters as resolved by lb_create (kernel organisation and
  * tile chosen for LB_KERNEL_AUTO and tile 0 x 0) into *out.  Errors: LB_E_INVALID

@@ -47,6 +47,16 @@ lb_status lb_selftest_recip(int32_t device, const double *x, int64_t n, double *
  * Synchronous.  Errors: LB_E_INVALID (NULL flag, polls < 1), LB_E_NOMEM, LB_E_CUDA. */
 lb_status lb_selftest_wait(int32_t device, uint32_t polls, int32_t arrive, uint32_t *flag);
 
+/* The bounded wait of a chained step (lb_step with two or more steps, LB_FP32_DFMU /
+ * LB_FP32, two components, D2Q9) on a neighbouring tile's completion flag, run by one
+ * thread on device `device` against a flag that already holds the awaited step (set != 0)
+ * or never will (set == 0: it holds the step before, and nothing writes it).  The wait
+ * gives up after wait_ns nanoseconds of GPU time; *flag receives the error word: 0 when the
+ * flag was reached, 4 (the stall bit, reported as LB_E_TIMEOUT by lb_step) when the bound
+ * ran out.  No fault, no hang: the wait ends either way.  Synchronous.  Errors:
+ * LB_E_INVALID (NULL flag, wait_ns < 1 or > 10^10), LB_E_NOMEM, LB_E_CUDA. */
+lb_status lb_selftest_flag_wait(int32_t device, uint64_t wait_ns, int32_t set, uint32_t *flag);
+
 #ifdef __cplusplus
 }
 #endif

@@ -129,6 +129,11 @@ class Simulation:
         return capi.lb_launch_count(self.ctx)
 
     @property
+    def chain_rows(self):
+        """Tile rows of a chained step that set flags (0: lb_step does not chain)."""
+        return capi.lb_chain_rows(self.ctx)
+
+    @property
     def kernel(self):
         """Organisation of the step kernel chosen by lb_create: ("tiles" or "strips", tile)."""
         p = capi.lb_get_params(self.ctx)

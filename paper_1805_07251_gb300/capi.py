@@ -99,6 +99,7 @@ def load():
         "lb_load_state": (ctypes.c_int, [C, C, ctypes.c_size_t]),
         "lb_step_count": (ctypes.c_int64, [C]),
         "lb_launch_count": (ctypes.c_int64, [C]),
+        "lb_chain_rows": (ctypes.c_int32, [C]),
         "lb_get_params": (ctypes.c_int, [C, ctypes.POINTER(lb_params)]),
         "lb_destroy": (ctypes.c_int, [C]),
         "lb_status_str": (ctypes.c_char_p, [ctypes.c_int]),
@@ -107,6 +108,8 @@ def load():
         "lb_selftest_recip": (ctypes.c_int, [ctypes.c_int32, _DP, ctypes.c_int64, _DP]),
         "lb_selftest_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.c_uint32, ctypes.c_int32,
                                             ctypes.POINTER(ctypes.c_uint32)]),
+        "lb_selftest_flag_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32,
+                                                 ctypes.POINTER(ctypes.c_uint32)]),
         "lb_free_energy_noalloc": (ctypes.c_int, [P, C, C]),
         "lb_batch_create": (ctypes.c_int, [P, ctypes.POINTER(lb_run_desc), ctypes.c_int32, ctypes.POINTER(C)]),
         "lb_batch_init": (ctypes.c_int, [C, _DP]),
@@ -217,6 +220,10 @@ def lb_launch_count(ctx):
     return int(load().lb_launch_count(ctx))
 
 
+def lb_chain_rows(ctx):
+    return int(load().lb_chain_rows(ctx))
+
+
 def lb_get_params(ctx):
     p = lb_params()
     _check(ctx, load().lb_get_params(ctx, ctypes.byref(p)), "lb_get_params")
@@ -236,6 +243,14 @@ def lb_selftest_wait(device, polls, arrive):
     rc = load().lb_selftest_wait(int(device), int(polls), int(arrive), ctypes.byref(flag))
     if rc != LB_OK:
         raise LBError(rc, "lb_selftest_wait")
+    return int(flag.value)
+
+
+def lb_selftest_flag_wait(device, wait_ns, set_flag):
+    flag = ctypes.c_uint32(0)
+    rc = load().lb_selftest_flag_wait(int(device), int(wait_ns), int(set_flag), ctypes.byref(flag))
+    if rc != LB_OK:
+        raise LBError(rc, "lb_selftest_flag_wait")
     return int(flag.value)
 
 

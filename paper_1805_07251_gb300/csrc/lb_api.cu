@@ -90,6 +90,50 @@ namespace {
 
 cudaError_t run_step(lb_ctx *c) { return lb_ctx_step(c, c->f[c->cur], c->f[c->cur ^ 1]); }
 
+// Bound of one wait for a neighbouring tile's flag in a chained step (a tile takes
+// microseconds; the bound only turns a fault into an error instead of a hang).
+constexpr unsigned long long CHAIN_WAIT_NS = 1000000000ull;
+
+// Whether lb_step chains consecutive steps of this configuration (lb_chain.cuh): the
+// two-component FP32 lane-pair step on 32 x 8 tiles, with every ragged tile at least 3
+// nodes wide and high so that a tile's step touches only the 3 x 3 tiles around it.
+bool chain_eligible(const lb_params &p) {
+    const int rx = p.nx % 32, ry = p.ny % 8;
+    return p.lattice == LB_D2Q9 && p.ncomp == 2 && (p.precision == LB_FP32_DFMU || p.precision == LB_FP32) &&
+           p.kernel == LB_KERNEL_TILES && p.tile_x == 32 && p.tile_y == 8 && (rx == 0 || rx >= 3) &&
+           (ry == 0 || ry >= 3);
+}
+
+// Step `k` of a chain of `n` (lb_chain.cuh).
+cudaError_t run_chain_step(lb_ctx *c, int64_t k, int64_t n) {
+    StepLaunch a;
+    a.fin = c->f[c->cur];
+    a.fout = c->f[c->cur ^ 1];
+    a.P = c->dp;
+    a.ncomp = c->p.ncomp;
+    a.force = c->p.force_method | (lb_ctx_mrt(c) ? 2 : 0);
+    a.tile_x = c->p.tile_x;
+    a.tile_y = c->p.tile_y;
+    a.kernel = c->p.kernel;
+    a.stream = c->stream;
+    const int rows = (c->p.ny + 7) / 8;
+    ChainArgs ca;
+    ca.flag = c->chain_flag;
+    ca.step = c->chain_step;
+    ca.chained = k > 0 ? 1 : 0;
+    ca.flag_rows = c->chain_rows;
+    ca.release_rows = k + 1 < n ? c->chain_rows : 0;
+    ca.roff = c->chain_roff;
+    ca.wait_ns = CHAIN_WAIT_NS;
+    const bool pdl = k > 0;
+    cudaError_t e = c->p.precision == LB_FP32 ? d2q9_f32mu_chain(a, ca, pdl) : d2q9_df_chain(a, ca, pdl);
+    if (e == cudaSuccess) {
+        c->chain_step += 1u;
+        c->chain_roff = (c->chain_roff + 1) % rows;
+    }
+    return e;
+}
+
 FieldLaunch field_args(lb_ctx *c) {
     FieldLaunch a;
     a.f = c->f[c->cur];
@@ -122,6 +166,7 @@ lb_status sync_check(lb_ctx *c) {
     LB_CUDA(c, cudaMemcpyAsync(&h, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(c, cudaStreamSynchronize(c->stream));
     if (h & ERR_TIMEOUT) return fail(c, LB_E_TIMEOUT, "a step kernel's wait for its bulk copies ran out");
+    if (h & ERR_STALL) return fail(c, LB_E_TIMEOUT, "a chained step's wait for a neighbouring tile ran out");
     if (h & ERR_DOMAIN) return fail(c, LB_E_DOMAIN, "a density or eta <= 0, or a non-finite value, was met");
     return LB_OK;
 }
@@ -401,6 +446,25 @@ lb_status lb_create(const lb_params *p, lb_ctx **out) {
         lb_destroy(c);
         return LB_E_CUDA;
     }
+    if (chain_eligible(c->p)) {
+        // flags of every tile (zero: no chain step done), and the CTA rows of a step that
+        // set them: the rows of one wave of the chain kernel (its resident CTAs) plus the
+        // two rows the next step's first CTAs reach beyond them, plus one
+        const int tx = (p->nx + 31) / 32, ty = (p->ny + 7) / 8;
+        int sms = 0, dev = 0;
+        const int per_sm = p->precision == LB_FP32 ? d2q9_f32mu_chain_ctas_per_sm() : d2q9_df_chain_ctas_per_sm();
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1 ||
+            cudaMalloc(&c->chain_flag, sizeof(unsigned) * (size_t)tx * ty) != cudaSuccess ||
+            cudaMemset(c->chain_flag, 0, sizeof(unsigned) * (size_t)tx * ty) != cudaSuccess) {
+            cudaGetLastError();
+            lb_destroy(c);
+            return LB_E_NOMEM;
+        }
+        const int wave_rows = (per_sm * sms + tx - 1) / tx;
+        c->chain_rows = wave_rows + 3 < ty ? wave_rows + 3 : ty;
+        c->chain_step = 1u;
+    }
     *out = c;
     return LB_OK;
 }
@@ -497,8 +561,24 @@ lb_status lb_step(lb_ctx *c, int64_t nsteps) {
     DeviceGuard dg(c->p.device);
     LB_CUDA(c, dg.status);
     if (nsteps < 0) return fail(c, LB_E_INVALID, "nsteps < 0");
+    // two or more steps of a chaining configuration: one chain (lb_chain.cuh), cut where
+    // the host checks the error word
+    const bool chain = c->chain_flag != nullptr && nsteps >= 2;
+    int64_t k = 0;  // step within the current chain
     for (int64_t t = 0; t < nsteps; ++t) {
-        cudaError_t e = run_step(c);
+        cudaError_t e;
+        if (chain) {
+            int64_t left = nsteps - t;
+            if (c->p.check_every > 0) {
+                const int64_t to_check = c->p.check_every - c->steps % c->p.check_every;
+                if (to_check < left) left = to_check;
+            }
+            // a chain of one step is the plain step
+            e = (k == 0 && left == 1) ? run_step(c) : run_chain_step(c, k, k + left);
+            k = left == 1 ? 0 : k + 1;
+        } else {
+            e = run_step(c);
+        }
         if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
         c->cur ^= 1;
         c->steps += 1;
@@ -629,6 +709,8 @@ int64_t lb_step_count(const lb_ctx *c) { return c ? c->steps : -1; }
 
 int64_t lb_launch_count(const lb_ctx *c) { return c ? c->launches : -1; }
 
+int32_t lb_chain_rows(const lb_ctx *c) { return c ? (c->chain_flag ? c->chain_rows : 0) : -1; }
+
 lb_status lb_get_params(const lb_ctx *c, lb_params *out) {
     if (!c || !out) return LB_E_INVALID;
     *out = c->p;
@@ -648,6 +730,7 @@ lb_status lb_destroy(lb_ctx *c) {
     cudaFree(c->diag);
     cudaFree(c->err);
     cudaFree(c->tbl);
+    cudaFree(c->chain_flag);
     for (void *q : c->ckpt) cudaFree(q);
     delete c;
     return LB_OK;

@@ -27,6 +27,13 @@ struct lb_ctx {
     lbvdw::LogTables *tbl = nullptr;  // device copy of the log tables
     cudaStream_t stream = nullptr;
     lbvdw::DevParams dp{};
+    // chained steps (lb_chain.cuh): per-tile completion flags (nullptr: the context's
+    // configuration does not chain), the next chain step number, the row rotation of the
+    // next step, and the CTA rows of a step that set flags
+    unsigned *chain_flag = nullptr;
+    unsigned chain_step = 0;
+    int chain_roff = 0;
+    int chain_rows = 0;
     int64_t steps = 0, launches = 0;
     bool has_state = false, poisoned = false;
     std::string msg;

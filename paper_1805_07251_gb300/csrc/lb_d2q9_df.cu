@@ -6,4 +6,5 @@
 #define LBVDW_NAME d2q9_df
 #define LBVDW_STRIPS 1
 #define LBVDW_WS 1
+#define LBVDW_CHAIN 1
 #include "lb_tu.cuh"

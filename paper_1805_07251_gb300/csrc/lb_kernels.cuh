@@ -28,6 +28,7 @@ namespace lbvdw {
 
 constexpr unsigned ERR_DOMAIN = 1u;   // rho^c <= 0, eta <= 0 or non-finite value
 constexpr unsigned ERR_TIMEOUT = 2u;  // a bounded wait for bulk copies ran out (lb_strip.cuh)
+constexpr unsigned ERR_STALL = 4u;    // a bounded wait for a neighbouring tile's flag ran out (lb_chain.cuh)
 
 struct DevParams {
     int nx, ny;
@@ -906,7 +907,16 @@ struct PairPath {
 // forces, populations) and is computed by the packed FP32x2 instructions; shared memory
 // holds the pairs interleaved, so one 8-byte (16-byte for double-float mu) access moves
 // both components.  Same arithmetic as the general step_tile below, bitwise.
-template <int LAT, int NP, int TX, int TY, int FORCE, int MU>
+// A load of a stored population: plain (LD = 0; the read-only path where the compiler can
+// prove it) or cached in L2 only (LD = 1), for the chained steps of lb_chain.cuh, whose
+// input may still be written by the previous step's grid while this one runs.
+template <int LD>
+__device__ __forceinline__ float ld_pop(const float *p) {
+    if constexpr (LD == 1) return __ldcg(p);
+    else return *p;
+}
+
+template <int LAT, int NP, int TX, int TY, int FORCE, int MU, int LD = 0>
 __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, float *__restrict__ fout,
                                                const DevParams &P, int x0, int y0) {
     using L = Lat<LAT>;
@@ -947,8 +957,8 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
     const unsigned pl = (unsigned)plane;
     // element e of plane i of component c, from the node offset o of plane 0
     auto ld = [&](int c, int i, unsigned o) -> float {
-        if constexpr (NP == 1) return (fin + c * cq)[i * pl + o];
-        else return fin[(size_t)c * cq + (size_t)i * plane + o];
+        if constexpr (NP == 1) return ld_pop<LD>(&(fin + c * cq)[i * pl + o]);
+        else return ld_pop<LD>(&fin[(size_t)c * cq + (size_t)i * plane + o]);
     };
     // ---- phase 1a: own node -> shared (populations, densities) ------------------
     float2 jx[NP], jy[NP];
@@ -1079,7 +1089,7 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
             if constexpr (STAGE) gr[q][i] = s_g[i][tid];
             else if constexpr (RELOAD) {
                 const float *sq = fin + (size_t)y * nx + x + 2 * q * cq;
-                gr[q][i] = make_float2(sq[(size_t)i * plane], sq[cq + (size_t)i * plane]);
+                gr[q][i] = make_float2(ld_pop<LD>(&sq[(size_t)i * plane]), ld_pop<LD>(&sq[cq + (size_t)i * plane]));
             } else gr[q][i] = gk[q][i];
         }
     collide_pairs<LAT, NP, FORCE>(rho, lap, gpx, gpy, grx, gry, jx, jy, P, gr, post);

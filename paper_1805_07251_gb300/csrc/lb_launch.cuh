@@ -2,6 +2,7 @@
 // Each lattice/precision pair lives in its own .cu file so the library builds in
 // parallel; lb_api.cu dispatches to them.
 #pragma once
+#include "lb_chain.cuh"
 #include "lb_device_guard.cuh"
 #include "lb_kernels.cuh"
 #include "lbvdw.h"
@@ -57,6 +58,12 @@ cudaError_t d2q9_df_strip(const StepLaunch &a);
 cudaError_t d2q9_f32mu_strip(const StepLaunch &a);
 cudaError_t d2q9_df_ws(const StepLaunch &a);
 cudaError_t d2q9_f32mu_ws(const StepLaunch &a);
+// chained steps (lb_chain.cuh): one step of a chain, launched with programmatic
+// serialisation after the previous one when `pdl`; CTAs of the chain kernel resident per SM
+cudaError_t d2q9_df_chain(const StepLaunch &a, const ChainArgs &ca, bool pdl);
+cudaError_t d2q9_f32mu_chain(const StepLaunch &a, const ChainArgs &ca, bool pdl);
+int d2q9_df_chain_ctas_per_sm();
+int d2q9_f32mu_chain_ctas_per_sm();
 
 // field launchers: one per lattice and storage type (double / float)
 #define LBVDW_DECLARE_FIELDS(NAME)                         \

@@ -2,6 +2,7 @@
 // (include/lbvdw_selftest.h).
 #include <cstring>
 
+#include "lb_chain.cuh"
 #include "lb_device_guard.cuh"
 #include "lb_kernels.cuh"
 #include "lb_strip.cuh"
@@ -48,7 +49,38 @@ __global__ void selftest_wait_kernel(unsigned *flag, unsigned polls, int arrive)
     if (!lbvdw::mbar_wait_bounded(&bar, 0, polls)) atomicOr(flag, lbvdw::ERR_TIMEOUT);
 }
 
+// The bounded flag wait of the chained steps: one thread waits for flag[0] to reach
+// `step`; a wait that runs out sets the stall bit in *err.
+__global__ void selftest_flag_wait_kernel(const unsigned *flag, unsigned step, unsigned long long wait_ns,
+                                          unsigned *err) {
+    if (threadIdx.x == 0) lbvdw::wait_flag(flag, 0, step, wait_ns, err);
+}
+
 }  // namespace
+
+extern "C" lb_status lb_selftest_flag_wait(int32_t device, uint64_t wait_ns, int32_t set, uint32_t *flag) {
+    if (!flag || wait_ns < 1 || wait_ns > 10000000000ull) return LB_E_INVALID;
+    lbvdw::DeviceGuard dg(device);
+    if (!dg.ok()) return LB_E_CUDA;
+    unsigned *d = nullptr;  // [0] the awaited flag, [1] the error word
+    if (cudaMalloc(&d, 2 * sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return LB_E_NOMEM;
+    }
+    const unsigned step = 7u;
+    const unsigned h[2] = {set ? step : step - 1u, 0u};
+    lb_status st = LB_OK;
+    if (cudaMemcpy(d, h, sizeof h, cudaMemcpyHostToDevice) != cudaSuccess) {
+        st = LB_E_CUDA;
+    } else {
+        selftest_flag_wait_kernel<<<1, 32>>>(d, step, (unsigned long long)wait_ns, d + 1);
+        if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+            cudaMemcpy(flag, d + 1, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = LB_E_CUDA;
+    }
+    cudaFree(d);
+    return st;
+}
 
 extern "C" lb_status lb_selftest_wait(int32_t device, uint32_t polls, int32_t arrive, uint32_t *flag) {
     if (!flag || polls < 1) return LB_E_INVALID;

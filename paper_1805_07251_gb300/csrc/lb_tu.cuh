@@ -105,6 +105,42 @@ cudaError_t LBVDW_CAT(LBVDW_NAME, _step)(const StepLaunch &a) {
 #endif
 }
 
+#ifdef LBVDW_CHAIN
+
+cudaError_t LBVDW_CAT(LBVDW_NAME, _chain)(const StepLaunch &a, const ChainArgs &ca, bool pdl) {
+    if (a.ncomp != 2 || a.tile_x != 32 || a.tile_y != 8) return cudaErrorInvalidConfiguration;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((a.P.nx + 31) / 32, (a.P.ny + 7) / 8);
+    cfg.blockDim = dim3(32, 8);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = a.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    const float *fin = static_cast<const float *>(a.fin);
+    float *fout = static_cast<float *>(a.fout);
+    switch (a.force) {
+        case 0: return cudaLaunchKernelEx(&cfg, lb_chain_kernel<0, MUV>, fin, fout, a.P, ca);
+        case 1: return cudaLaunchKernelEx(&cfg, lb_chain_kernel<1, MUV>, fin, fout, a.P, ca);
+        case 2: return cudaLaunchKernelEx(&cfg, lb_chain_kernel<2, MUV>, fin, fout, a.P, ca);
+        case 3: return cudaLaunchKernelEx(&cfg, lb_chain_kernel<3, MUV>, fin, fout, a.P, ca);
+    }
+    return cudaErrorInvalidConfiguration;
+}
+
+int LBVDW_CAT(LBVDW_NAME, _chain_ctas_per_sm)() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, lb_chain_kernel<0, MUV>, 256, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+#endif
+
 #ifdef LBVDW_STRIPS
 
 namespace {
