@@ -68,25 +68,26 @@ def parse(argv=None):
                     help="adjoint rollouts: steps of the rollout (0: the workload's 2000)")
     ap.add_argument("--no-fd", action="store_true",
                     help="adjoint rollouts: skip the finite-difference checks (profiling runs)")
-    ap.add_argument("--only", choices=["fp32_dfmu", "fp32_mixed", "fp32", "fp64", "sweep", "c4", "adjoint", "c1"],
+    ap.add_argument("--only", choices=["fp32_dfmu", "fp32_mixed", "fp32", "fp64", "sweep", "c4", "adjoint", "c1",
+                                       "sizes"],
                     default=None,
-                    help="time one path only (profiling runs): no e2e, no cpu baseline")
+                    help="time one path only (profiling runs): no e2e, no cpu baseline; 'sizes': the headline "
+                         "path on lattices of 512^2 to 4096^2 of the same recipe")
     return ap.parse_args(argv)
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the headline
 # step kernel (the chained step), from an ncu capture of this script (the profile file
-# named beside it).  The
-# value holds for the kernel sources whose digest is recorded with it and is reported as
-# null once they change.
+# named beside it).  The value holds for the kernel sources whose digest is recorded with
+# it and is reported as null once they change.
 KERNEL_SOURCES = ("lb_kernels.cuh", "lb_chain.cuh", "lb_lane.cuh", "lb_mu.cuh", "lb_tu.cuh", "lb_launch.cuh",
                   "lb_d2q9_df.cu")
-TRAFFIC = {"fp32_dfmu": {"digest": "2137365bdf95ec855ec85c16525185470f30a20634a5c9c75b9f7f2686518a6e",
-                         "bytes": 108305920, "warp_instructions": 27213824, "issue_active": 0.558,
-                         "fma_pipe_active": 0.536,
-                         "stalls_per_issue": {"barrier": 2.94, "not_selected": 2.70, "long_scoreboard": 2.49,
-                                              "math_pipe_throttle": 2.41, "mio_throttle": 1.17},
-                         "profile": "profiles/lb_step_kernel_fp32_dfmu_c2_1024.md"}}
+TRAFFIC = {"fp32_dfmu": {"digest": "74c6e37d6beedf425343622e22eaff4b72b14132c649bbde6aecadb69663e178",
+                         "bytes": 108860672, "warp_instructions": 29557472, "issue_active": 0.584,
+                         "fma_pipe_active": 0.517,
+                         "stalls_per_issue": {"barrier": 2.92, "long_scoreboard": 2.66, "not_selected": 2.47,
+                                              "math_pipe_throttle": 2.14, "wait": 1.24},
+                         "profile": "profiles/lb_chain_kernel_fp32_dfmu_c2_1024.md"}}
 # instruction issue peak of the GPU: 152 SMs x 4 schedulers x 2.07 GHz (one warp instruction
 # per scheduler per cycle)
 ISSUE_PEAK = 152 * 4 * 2.07e9
@@ -583,6 +584,40 @@ def time_path(torch, Simulation, kw, rho, precision, steps, warmup, flush, dev):
     return sim, ev, launches0, stream
 
 
+def time_sizes(torch, Simulation, dev, steps, warmup, flush):
+    """The headline path (FP32 storage, double-float mu) on square lattices of the c2 recipe
+    from 512^2 to 4096^2: K steps back to back in one lb_step call, and one launch per step
+    with the L2 flushed before each.  What does not scale with the lattice (launch, the
+    first wave of CTAs, the last) shows as the difference between the sizes."""
+    import lbinputs
+
+    p = lbinputs.base_params(WORKLOAD)
+    peak_gbs, _ = read_peaks()
+    out = {}
+    for n in (512, 1024, 2048, 4096):
+        kw = lbinputs.lib_kwargs(p, nx=n, ny=n)
+        rho = lbinputs.fields(WORKLOAD, n, n)
+        sim, ev, _, stream = time_path(torch, Simulation, kw, rho, "fp32_dfmu", steps, warmup, flush, dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            sim.step(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        job = e0.elapsed_time(e1) / steps * 1e-3
+        fl = sum(a.elapsed_time(b) for a, b in ev) / steps * 1e-3
+        alg = 2 * n * n * 9 * 2 * 4
+        out[str(n)] = {"nodes": n * n, "chain_rows": sim.chain_rows,
+                       "job_us_per_step": job * 1e6, "job_frac": alg / job / 1e9 / peak_gbs,
+                       "flushed_us_per_step": fl * 1e6, "flushed_frac": alg / fl / 1e9 / peak_gbs}
+        sim.close()
+    return {"sizes": out, "peak_gbs": peak_gbs, "steps": steps}
+
+
 def kernel_for(precision):
     """The requested kernel organisation where it applies to the precision, else the
     library's choice (strips: FP32 storage; warp-specialised tiles: FP32-class mu)."""
@@ -639,9 +674,11 @@ def main():
 
     results = {}
     clocks = None
-    if args.only in ("sweep", "c4", "adjoint", "c1"):
+    if args.only in ("sweep", "c4", "adjoint", "c1", "sizes"):
         # profiling runs of one secondary workload: its JSON object alone
-        if args.only == "sweep":
+        if args.only == "sizes":
+            out = time_sizes(torch, Simulation, dev, args.steps, args.warmup, flush)
+        elif args.only == "sweep":
             out = time_sweep(torch, dev, "fp32_dfmu", args.steps, args.warmup, dist)
         elif args.only == "c4":
             out = time_c4(torch, dev, "fp32_dfmu", args.steps, args.warmup)
