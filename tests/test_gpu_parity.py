@@ -8,6 +8,7 @@ import pytest
 
 import lbinputs
 import oracle
+from oracle_windows import oracle_two_steps_at
 
 pytestmark = pytest.mark.gpu
 
@@ -282,6 +283,44 @@ def test_fp32_full_size_sampled_one_step(gpu_lib, parity_bound, config, precisio
         ro, jo = win.moments(win.run(win.equilibrium(rho[:, ys][:, :, xs]), 1))
         worst = max(worst, np.max(np.abs(r_g[:, y, x] - ro[:, 4, 4])), np.max(np.abs(j_g[:, :, y, x] - jo[:, :, 4, 4])))
     parity_bound("first step, rho and j", worst, bar)
+
+
+D2Q9_W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+def test_fp32_full_size_chained_steps_restart_against_oracle(gpu_lib, parity_bound):
+    # the headline's launch configuration: 1024^2, two components, FP32 deviation storage
+    # with double-float mu, consecutive steps of one lb_step call (chained launches: the
+    # first CTA rows wait on neighbouring tiles' flags, the others on the whole previous
+    # grid).  At steps 0 and 300 of the GPU's own chained trajectory, two chained GPU steps
+    # against two FP64 oracle steps restarted from the GPU's state (f = g + w_i rho_ref) at
+    # sampled nodes.  The GPU steps in FP32: the bar is FP32 rounding.
+    p = lbinputs.base_params("c2")
+    rho = lbinputs.fields("c2")
+    rref = np.array([float(np.float32(rho[c].mean())) for c in range(2)])
+    sim, _ = make_pair(p, precision="fp32_dfmu", rho_ref=rref)
+    assert sim.kernel == ("tiles", (32, 8)) and sim.chain_rows > 0
+    kw = lbinputs.lib_kwargs(p)
+    win9 = oracle.Lattice("D2Q9", 9, 9, 2, kw["tau"], kw["kT"], kw["gamma_mu"], kw["a"], kw["kappa"],
+                          kw["lam"], kw["b"])
+    fshape = (2, 9, 1024, 1024)
+    r = np.random.default_rng(81)
+    sim.init(rho)
+    done = 0
+    for t in (0, 300):
+        sim.step(t - done)
+        g = gpu_populations(sim, fshape, dtype=np.float32)
+        f_t = g.astype(np.float64) + D2Q9_W[None, :, None, None] * rref[:, None, None, None]
+        sim.step(2)
+        done = t + 2
+        r_g, j_g = sim.moments()
+        pts = [(0, 0), (1023, 1023), (512, 0), (0, 777), (7, 31), (8, 32), (215, 500)]
+        pts += [tuple(int(v) for v in r.integers(0, 1024, 2)) for _ in range(25)]
+        worst = 0.0
+        for (y, x) in pts:
+            ro, jo = oracle_two_steps_at(win9, f_t, y, x)
+            worst = max(worst, float(np.max(np.abs(r_g[:, y, x] - ro))), float(np.max(np.abs(j_g[:, :, y, x] - jo))))
+        parity_bound(f"two chained steps at {t}, rho and j", worst, 1e-6)
 
 
 def test_free_energy_diagnostic_matches_oracle(gpu_lib):

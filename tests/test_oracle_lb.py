@@ -660,3 +660,25 @@ def test_mrt_low_shear_viscosity_stays_stable_where_bgk_does_not():
     assert grows(tau=0.6)
     assert not grows(tau=1.0, tau_s=0.6, tau_g=1.0)
     assert grows(tau=1.0, tau_s=1.2, tau_g=1.0)
+
+
+def test_two_step_window_reference_equals_direct_two_steps():
+    """The exact two-step reference that the full-size chained GPU test builds from one-step
+    9 x 9 windows (tests/oracle_windows.py) equals two oracle steps of the whole periodic
+    lattice at every sampled node."""
+    import lbinputs
+    from oracle_windows import oracle_two_steps_at
+
+    p = lbinputs.base_params("c2")
+    kw = lbinputs.lib_kwargs(p)
+    n = 24
+    rho = lbinputs.fields("c2", n, n)
+    lat = oracle.Lattice("D2Q9", n, n, 2, kw["tau"], kw["kT"], kw["gamma_mu"], kw["a"], kw["kappa"], kw["lam"],
+                         kw["b"])
+    f0 = lat.run(lat.equilibrium(rho), 50)
+    r2, j2 = lat.moments(lat.run(f0, 2))
+    win9 = oracle.Lattice("D2Q9", 9, 9, 2, kw["tau"], kw["kT"], kw["gamma_mu"], kw["a"], kw["kappa"], kw["lam"],
+                          kw["b"])
+    for (y, x) in [(0, 0), (5, 17), (23, 23), (11, 3)]:
+        ro, jo = oracle_two_steps_at(win9, f0, y, x)
+        assert np.array_equal(ro, r2[:, y, x]) and np.array_equal(jo, j2[:, :, y, x])
