@@ -188,7 +188,8 @@ lb_status lb_init_fields_dev(lb_ctx *ctx, const double *rho_dev, const double *m
  * nodes wide and high): step s + 1 launches while step s is finishing, and a tile of step
  * s + 1 that starts early waits on completion flags of the 3 x 3 tiles around it instead
  * of on the whole grid.  The results are bitwise those of one launch per step; a chain is
- * cut where check_every synchronises, and a single step is always one plain launch.  A
+ * cut where check_every synchronises, a single step is always one plain launch, and steps
+ * enqueued while the stream is being captured into a CUDA graph are plain launches.  A
  * chained wait is bounded (one second); one that runs out sets the error word's stall bit.
  * Errors: LB_E_STATE, LB_E_INVALID, LB_E_CUDA, LB_E_DOMAIN and LB_E_TIMEOUT (only when
  * check_every > 0). */

@@ -562,8 +562,12 @@ lb_status lb_step(lb_ctx *c, int64_t nsteps) {
     LB_CUDA(c, dg.status);
     if (nsteps < 0) return fail(c, LB_E_INVALID, "nsteps < 0");
     // two or more steps of a chaining configuration: one chain (lb_chain.cuh), cut where
-    // the host checks the error word
-    const bool chain = c->chain_flag != nullptr && nsteps >= 2;
+    // the host checks the error word.  Not while the stream is being captured: a replayed
+    // graph would repeat the step numbers its launches were captured with, and flags left
+    // by an earlier replay would release tiles early.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    LB_CUDA(c, cudaStreamIsCapturing(c->stream, &cap));
+    const bool chain = c->chain_flag != nullptr && nsteps >= 2 && cap == cudaStreamCaptureStatusNone;
     int64_t k = 0;  // step within the current chain
     for (int64_t t = 0; t < nsteps; ++t) {
         cudaError_t e;

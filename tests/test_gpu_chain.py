@@ -119,3 +119,39 @@ def test_chains_continue_across_calls_and_reinitialisation(gpu_lib):
     finally:
         a.close()
         b.close()
+
+
+def test_steps_captured_in_a_cuda_graph_replay_like_single_steps(gpu_lib):
+    """lb_step enqueued while its stream is captured into a CUDA graph uses plain launches
+    (a replayed chain would reuse its captured step numbers); three replays of a captured
+    call of 4 steps equal 12 single steps."""
+    import torch
+
+    from paper_1805_07251_gb300 import Simulation
+
+    p = lbinputs.base_params("c2")
+    kw = lbinputs.lib_kwargs(p, nx=256, ny=256)
+    rho = lbinputs.fields("c2", 256, 256)
+    s = torch.cuda.Stream()
+    a = Simulation(precision="fp32_dfmu", device=0, stream=s.cuda_stream, **kw)
+    b = Simulation(precision="fp32_dfmu", device=0, **kw)
+    try:
+        assert a.chain_rows > 0
+        a.init(rho)
+        b.init(rho)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            a.step(4)
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        for _ in range(12):
+            b.step(1)
+        # populations only: the saved header holds the host's step count, which graph
+        # replays do not advance (4 against 12)
+        assert np.array_equal(a.save_state()[64:], b.save_state()[64:])
+        assert a.steps == 4 and b.steps == 12
+    finally:
+        a.close()
+        b.close()
