@@ -130,11 +130,22 @@ size_t resident_smem(int precision, int N, int L) {
 }
 
 // Enqueue `len` timesteps starting from pool[parity]: the D1Q3 runs in one resident
-// launch (result written to the pool the D2Q9 runs end in), then len tile launches.
-cudaError_t enqueue_chunk(lb_batch *b, int parity, int len) {
+// launch (result written to the pool the D2Q9 runs end in) and len tile launches.  When
+// `side` is given (both kinds of runs present, under capture), the resident launch goes on
+// a branch of its own, forked from and joined back into b->stream by the two events: the
+// D1Q3 and D2Q9 runs share no memory (their pool regions and error words are disjoint), so
+// the graph lets them run side by side.
+cudaError_t enqueue_chunk(lb_batch *b, int parity, int len, cudaStream_t side, cudaEvent_t fork,
+                          cudaEvent_t join) {
+    if (side) {
+        cudaError_t e = cudaEventRecord(fork, b->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
+        if (e != cudaSuccess) return e;
+    }
     if (!b->d1.empty()) {
         BatchLaunch a = launch_args(b, parity, len);
         a.pool_out = b->pool[parity ^ (len & 1)];
+        if (side) a.stream = side;
         cudaError_t e = launch_resident(b, a);
         if (e != cudaSuccess) return e;
     }
@@ -143,6 +154,11 @@ cudaError_t enqueue_chunk(lb_batch *b, int parity, int len) {
             cudaError_t e = launch_tiles(b, launch_args(b, parity ^ (s & 1), 0));
             if (e != cudaSuccess) return e;
         }
+    }
+    if (side) {
+        cudaError_t e = cudaEventRecord(join, side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, join, 0);
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -158,20 +174,31 @@ cudaError_t get_graph(lb_batch *b, int parity, int len, cudaGraphExec_t *out) {
         *out = it->second;
         return cudaSuccess;
     }
-    cudaStream_t cap = nullptr;
+    cudaStream_t cap = nullptr, side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    const bool both = !b->d1.empty() && b->ntiles > 0;
     cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return e;
-    cudaStream_t saved = b->stream;
-    b->stream = cap;
-    cudaGraph_t g = nullptr;
-    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        cudaError_t e2 = enqueue_chunk(b, parity, len);
-        e = cudaStreamEndCapture(cap, &g);
-        if (e2 != cudaSuccess) e = e2;
+    if (e == cudaSuccess && both) {
+        e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
     }
-    b->stream = saved;
-    cudaStreamDestroy(cap);
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) {
+        cudaStream_t saved = b->stream;
+        b->stream = cap;
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e2 = enqueue_chunk(b, parity, len, side, fork, join);
+            e = cudaStreamEndCapture(cap, &g);
+            if (e2 != cudaSuccess) e = e2;
+        }
+        b->stream = saved;
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (side) cudaStreamDestroy(side);
+    if (cap) cudaStreamDestroy(cap);
     if (e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         return e;
