@@ -21,13 +21,26 @@ struct BatchTile {
     int run, x0, y0, pad;
 };
 
+// Copy a run's parameter block into shared memory (the single-run kernels get theirs as a
+// kernel parameter, whose fields the arithmetic reads for free; read from global memory
+// they would be loads on the critical path).  The caller synchronises before use.
+__device__ __forceinline__ void stage_params(DevParams &dst, const DevParams *src, int tid, int nthreads) {
+    static_assert(sizeof(DevParams) % 8 == 0, "DevParams in 8-byte words");
+    const int2 *s = reinterpret_cast<const int2 *>(src);
+    int2 *d = reinterpret_cast<int2 *>(&dst);
+    for (int k = tid; k < (int)(sizeof(DevParams) / 8); k += nthreads) d[k] = s[k];
+}
+
 template <int N, int TX, int TY, class S, class R, int FORCE, int MU>
 __global__ void __launch_bounds__(TX *TY, MinBlocks<S, N, TX * TY, PairPath<N, S, R, MU>::value>::value)
     lb_batch_tile_kernel(const S *__restrict__ pool_in, S *__restrict__ pool_out, const DevParams *__restrict__ runs,
                          const size_t *__restrict__ offsets, const BatchTile *__restrict__ tiles) {
     const BatchTile t = tiles[blockIdx.x];
     const size_t off = offsets[t.run];
-    step_tile<2, N, TX, TY, S, R, FORCE, MU>(pool_in + off, pool_out + off, runs[t.run], t.x0, t.y0);
+    __shared__ __align__(16) DevParams s_p;
+    stage_params(s_p, runs + t.run, threadIdx.x + TX * threadIdx.y, TX * TY);
+    __syncthreads();
+    step_tile<2, N, TX, TY, S, R, FORCE, MU>(pool_in + off, pool_out + off, s_p, t.x0, t.y0);
 }
 
 // Largest D1Q3 run the resident kernel holds, and its thread count.
@@ -53,9 +66,12 @@ __global__ void __launch_bounds__(RESIDENT_THREADS)
     constexpr int NT = RESIDENT_THREADS;
     constexpr int MAXM = RESIDENT_MAX_NODES_PER_THREAD;
     const int run = run_ids[blockIdx.x];
-    const DevParams &P = runs[run];
-    const int L = P.nx;
     const int tid = threadIdx.x;
+    __shared__ __align__(16) DevParams s_p;
+    stage_params(s_p, runs + run, tid, RESIDENT_THREADS);
+    __syncthreads();
+    const DevParams &P = s_p;
+    const int L = P.nx;
 
     extern __shared__ __align__(16) unsigned char smem[];
     // layout: tables | phi [N][L+2] | rho [N][L+4] | f [N][3][L]

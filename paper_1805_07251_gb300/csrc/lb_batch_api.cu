@@ -279,7 +279,8 @@ lb_status lb_batch_create(const lb_params *shared, const lb_run_desc *runs, int3
     b->pool_elems = off;
     if (maxL1 > 0) {
         b->smem = resident_smem(shared->precision, N, maxL1);
-        if (b->smem > 227 * 1024) {
+        // dynamic shared memory plus the kernel's static copy of the run's parameters
+        if (b->smem + sizeof(DevParams) > 227 * 1024) {
             delete b;
             return LB_E_INVALID;  // the longest D1Q3 run does not fit one CTA's shared memory
         }
