@@ -17,8 +17,11 @@
 
 namespace lbvdw {
 
+// One tile of the flat work list: its run, origin, the run's lattice size and the run's
+// element offset in the pools (what the tile needs before its parameter block arrives).
 struct BatchTile {
-    int run, x0, y0, pad;
+    int run, x0, y0, nx, ny, pad;
+    size_t off;
 };
 
 // Copy a run's parameter block into shared memory (the single-run kernels get theirs as a
@@ -34,13 +37,28 @@ __device__ __forceinline__ void stage_params(DevParams &dst, const DevParams *sr
 template <int N, int TX, int TY, class S, class R, int FORCE, int MU>
 __global__ void __launch_bounds__(TX *TY, MinBlocks<S, N, TX * TY, PairPath<N, S, R, MU>::value>::value)
     lb_batch_tile_kernel(const S *__restrict__ pool_in, S *__restrict__ pool_out, const DevParams *__restrict__ runs,
-                         const size_t *__restrict__ offsets, const BatchTile *__restrict__ tiles) {
+                         const BatchTile *__restrict__ tiles, const LogTables *__restrict__ tbl) {
     const BatchTile t = tiles[blockIdx.x];
-    const size_t off = offsets[t.run];
+    const int tid = threadIdx.x + TX * threadIdx.y;
     __shared__ __align__(16) DevParams s_p;
-    stage_params(s_p, runs + t.run, threadIdx.x + TX * threadIdx.y, TX * TY);
-    __syncthreads();
-    step_tile<2, N, TX, TY, S, R, FORCE, MU>(pool_in + off, pool_out + off, s_p, t.x0, t.y0);
+    if constexpr (PairPath<N, S, R, MU>::value) {
+        // the parameter block is requested here and stored once the tile's populations are
+        // requested too, so the two global round trips overlap
+        constexpr int W = (int)(sizeof(DevParams) / 8);
+        static_assert(sizeof(DevParams) % 8 == 0 && W <= TX * TY, "one 8-byte word of DevParams per thread");
+        int2 w = make_int2(0, 0);
+        if (tid < W) w = reinterpret_cast<const int2 *>(runs + t.run)[tid];
+        auto hook = [&]() {
+            if (tid < W) reinterpret_cast<int2 *>(&s_p)[tid] = w;
+            __syncthreads();
+        };
+        step_tile_pair<2, N / 2, TX, TY, FORCE, MU>(pool_in + t.off, pool_out + t.off, s_p, t.x0, t.y0,
+                                                    TileGeo{t.nx, t.ny, tbl}, hook);
+    } else {
+        stage_params(s_p, runs + t.run, tid, TX * TY);
+        __syncthreads();
+        step_tile<2, N, TX, TY, S, R, FORCE, MU>(pool_in + t.off, pool_out + t.off, s_p, t.x0, t.y0);
+    }
 }
 
 // Largest D1Q3 run the resident kernel holds, and its thread count.

@@ -74,7 +74,7 @@ cudaError_t build_tiles(lb_batch *b) {
     for (int r : b->d2) {
         const lb_run_desc &d = b->desc[r];
         for (int y0 = 0; y0 < d.ny; y0 += b->tile_y)
-            for (int x0 = 0; x0 < d.nx; x0 += b->tile_x) t.push_back({r, x0, y0, 0});
+            for (int x0 = 0; x0 < d.nx; x0 += b->tile_x) t.push_back({r, x0, y0, d.nx, d.ny, 0, b->offsets[r]});
     }
     cudaFree(b->d_tiles);
     b->d_tiles = nullptr;
@@ -92,6 +92,7 @@ BatchLaunch launch_args(lb_batch *b, int parity, int nsteps) {
     a.runs = b->d_params;
     a.offsets = b->d_offsets;
     a.tiles = b->d_tiles;
+    a.tbl = b->d_tbl;
     a.ntiles = b->ntiles;
     a.d1_ids = b->d_d1;
     a.nd1 = (int)b->d1.size();

@@ -10,6 +10,7 @@ struct BatchLaunch {
     const DevParams *runs;     // device array, one parameter block per run
     const size_t *offsets;     // device array, element offset of each run in the pools
     const BatchTile *tiles;    // device array of D2Q9 tiles
+    const LogTables *tbl;      // device log tables (shared by every run)
     int ntiles;
     const int *d1_ids;         // device array of D1Q3 run indices
     int nd1;

@@ -14,7 +14,7 @@ template <int N, int TX, int TY, int FORCE>
 cudaError_t tiles_one(const BatchLaunch &a) {
     if (a.ntiles == 0) return cudaSuccess;
     lb_batch_tile_kernel<N, TX, TY, SB, RB, FORCE, MUB><<<a.ntiles, dim3(TX, TY), 0, a.stream>>>(
-        static_cast<const SB *>(a.pool_in), static_cast<SB *>(a.pool_out), a.runs, a.offsets, a.tiles);
+        static_cast<const SB *>(a.pool_in), static_cast<SB *>(a.pool_out), a.runs, a.tiles, a.tbl);
     return cudaGetLastError();
 }
 

@@ -212,18 +212,23 @@ struct TblWords {
 };
 
 template <int MU>
-__device__ __forceinline__ void load_tables(float *s_tbl, const DevParams &P, int tid, int nt) {
+__device__ __forceinline__ void load_tables(float *s_tbl, const LogTables *tbl, int tid, int nt) {
     if constexpr (MU == MU_TBL) {
         double *t = reinterpret_cast<double *>(s_tbl);
         for (int k = tid; k < LOG_TBL; k += nt) {
-            t[k] = P.tbl->r64[k];
-            t[LOG_TBL + k] = P.tbl->t64_hi[k];
-            t[2 * LOG_TBL + k] = P.tbl->t64_lo[k];
+            t[k] = tbl->r64[k];
+            t[LOG_TBL + k] = tbl->t64_hi[k];
+            t[2 * LOG_TBL + k] = tbl->t64_lo[k];
         }
     } else if constexpr (MU == MU_DF) {
         float4 *t = reinterpret_cast<float4 *>(s_tbl);
-        for (int k = tid; k < LOG_TBL; k += nt) t[k] = P.tbl->t32[k];
+        for (int k = tid; k < LOG_TBL; k += nt) t[k] = tbl->t32[k];
     }
+}
+
+template <int MU>
+__device__ __forceinline__ void load_tables(float *s_tbl, const DevParams &P, int tid, int nt) {
+    load_tables<MU>(s_tbl, P.tbl, tid, nt);
 }
 
 // Moments of one node's populations (deviations): sum_i g_i and the bare momentum
@@ -902,11 +907,6 @@ struct PairPath {
     static constexpr bool value = N % 2 == 0 && sizeof(S) == 4 && sizeof(R) == 4 && (MU == MU_DF || MU == MU_F32);
 };
 
-// The fused step, FP32 components in lane pairs (NP pairs: components 2q and 2q+1 in pair q):
-// every per-node quantity of a pair lives in one register pair (densities, momenta, mu,
-// forces, populations) and is computed by the packed FP32x2 instructions; shared memory
-// holds the pairs interleaved, so one 8-byte (16-byte for double-float mu) access moves
-// both components.  Same arithmetic as the general step_tile below, bitwise.
 // A load of a stored population: plain (LD = 0; the read-only path where the compiler can
 // prove it) or cached in L2 only (LD = 1), for the chained steps of lb_chain.cuh, whose
 // input may still be written by the previous step's grid while this one runs.
@@ -916,9 +916,32 @@ __device__ __forceinline__ float ld_pop(const float *p) {
     else return *p;
 }
 
-template <int LAT, int NP, int TX, int TY, int FORCE, int MU, int LD = 0>
+// What a tile step needs before it reads its parameter block: the lattice size and the
+// log tables.  The single-run kernels take them from the parameter block itself (a kernel
+// parameter); the batched tile kernel from its tile entry, so that its populations are
+// requested while the run's parameter block is still on its way into shared memory.
+struct TileGeo {
+    int nx, ny;
+    const LogTables *tbl;
+};
+
+// The default hook of step_tile_pair: nothing between the node's loads and their use.
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+// The fused step, FP32 components in lane pairs (NP pairs: components 2q and 2q+1 in pair q):
+// every per-node quantity of a pair lives in one register pair (densities, momenta, mu,
+// forces, populations) and is computed by the packed FP32x2 instructions; shared memory
+// holds the pairs interleaved, so one 8-byte (16-byte for double-float mu) access moves
+// both components.  Same arithmetic as the general step_tile below, bitwise.
+// `hook` runs on every thread once the node's own populations are requested and before any
+// field of P but those in `geo` is read (the batched kernel completes its parameter block
+// in shared memory there).
+template <int LAT, int NP, int TX, int TY, int FORCE, int MU, int LD = 0, class Hook = NoHook>
 __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, float *__restrict__ fout,
-                                               const DevParams &P, int x0, int y0) {
+                                               const DevParams &P, int x0, int y0, const TileGeo geo,
+                                               const Hook &hook) {
     using L = Lat<LAT>;
     using G = TileGeom<LAT, TX, TY>;
     constexpr int Q = L::Q, HY = G::HY, EX = G::EX, MX = G::MX, MY = G::MY, NT = G::NT;
@@ -937,18 +960,16 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
     __shared__ PT s_phi[NP][MY * MX];
     __shared__ __align__(16) float s_tbl[TblWords<MU>::value];
 
-    const int nx = P.nx, ny = P.ny;
+    const int nx = geo.nx, ny = geo.ny;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = tx + TX * ty;
     const int x = x0 + tx, y = y0 + ty;
     const bool inside = x < nx && y < ny;
-    load_tables<MU>(s_tbl, P, tid, NT);
+    load_tables<MU>(s_tbl, geo.tbl, tid, NT);
     const size_t plane = (size_t)nx * (size_t)ny;
     const size_t cq = (size_t)Q * plane;  // component stride
     const bool small = nx <= TX + 1 || (LAT == 2 && ny <= TY + 1);
-    float2 rref[NP];
-#pragma unroll
-    for (int q = 0; q < NP; ++q) rref[q] = make_float2(P.rho_ref_f[2 * q], P.rho_ref_f[2 * q + 1]);
+    auto rref = [&](int q) { return make_float2(P.rho_ref_f[2 * q], P.rho_ref_f[2 * q + 1]); };
 
     // One pair: 32-bit element offsets within a component's Q planes (Q nx ny < 2^32 for
     // FP32 storage, checked when the context is created) from per-component base pointers,
@@ -970,13 +991,15 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
         for (int q = 0; q < NP; ++q) {
             float2 gv[Q], acc;
 #pragma unroll
+            for (int i = 0; i < Q; ++i) gv[i] = make_float2(ld(2 * q, i, off), ld(2 * q + 1, i, off));
+            if (q == 0) hook();
+#pragma unroll
             for (int i = 0; i < Q; ++i) {
-                gv[i] = make_float2(ld(2 * q, i, off), ld(2 * q + 1, i, off));
                 if constexpr (STAGE) s_g[i][tid] = gv[i];
                 else if constexpr (!RELOAD) gk[q][i] = gv[i];
             }
             moments_lane<LAT>(gv, acc, jx[q], jy[q]);
-            s_rho[q][(ty + 2 * HY) * EX + tx + 2] = v_add(rref[q], acc);
+            s_rho[q][(ty + 2 * HY) * EX + tx + 2] = v_add(rref(q), acc);
         }
     }
     // ---- phase 1b: densities on the 2-node ring ---------------------------------
@@ -991,7 +1014,7 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
             float2 acc = make_float2(ld(2 * q, 0, off), ld(2 * q + 1, 0, off));
 #pragma unroll
             for (int i = 1; i < Q; ++i) acc = v_add(acc, make_float2(ld(2 * q, i, off), ld(2 * q + 1, i, off)));
-            s_rho[q][ey * EX + ex] = v_add(rref[q], acc);
+            s_rho[q][ey * EX + ex] = v_add(rref(q), acc);
         }
     }
     __syncthreads();
@@ -1117,6 +1140,13 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
             }
         }
     }
+}
+
+// The lane-pair step with its geometry from the parameter block.
+template <int LAT, int NP, int TX, int TY, int FORCE, int MU, int LD = 0>
+__device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, float *__restrict__ fout,
+                                               const DevParams &P, int x0, int y0) {
+    step_tile_pair<LAT, NP, TX, TY, FORCE, MU, LD>(fin, fout, P, x0, y0, TileGeo{P.nx, P.ny, P.tbl}, NoHook());
 }
 
 // The fused step on one TX x TY tile with origin (x0, y0) of the lattice described by P.
