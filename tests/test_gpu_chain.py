@@ -155,3 +155,21 @@ def test_steps_captured_in_a_cuda_graph_replay_like_single_steps(gpu_lib):
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("n,steps", [(1024, 3000), (4096, 120)])
+def test_long_chains_bitwise_equal_single_steps(gpu_lib, n, steps):
+    """Long chains at the headline size (3000 steps in one call, the flag hand-off repeated
+    about 100,000 times) and on a lattice of 512 tile rows (9 of them handing over by flags),
+    bitwise against one plain launch per step: an ordering fault in the hand-off between
+    overlapping grids would show up as a difference here."""
+    a, b = _pair(n, n)
+    try:
+        assert a.chain_rows > 0
+        a.step(steps)
+        for _ in range(steps):
+            b.step(1)
+        assert np.array_equal(a.save_state()[64:], b.save_state()[64:])
+    finally:
+        a.close()
+        b.close()
