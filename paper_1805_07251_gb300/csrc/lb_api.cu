@@ -450,20 +450,30 @@ lb_status lb_create(const lb_params *p, lb_ctx **out) {
         // flags of every tile (zero: no chain step done), and the CTA rows of a step that
         // set them: the rows of one wave of the chain kernel (its resident CTAs) plus the
         // two rows the next step's first CTAs reach beyond them, plus one
+        // (a failed occupancy or device query leaves the context unchained: chaining only
+        // changes when tiles start, not what they compute)
         const int tx = (p->nx + 31) / 32, ty = (p->ny + 7) / 8;
         int sms = 0, dev = 0;
         const int per_sm = p->precision == LB_FP32 ? d2q9_f32mu_chain_ctas_per_sm() : d2q9_df_chain_ctas_per_sm();
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1 ||
-            cudaMalloc(&c->chain_flag, sizeof(unsigned) * (size_t)tx * ty) != cudaSuccess ||
-            cudaMemset(c->chain_flag, 0, sizeof(unsigned) * (size_t)tx * ty) != cudaSuccess) {
+        if (per_sm >= 1 && cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms >= 1) {
+            if (cudaMalloc(&c->chain_flag, sizeof(unsigned) * (size_t)tx * ty) != cudaSuccess) {
+                cudaGetLastError();
+                c->chain_flag = nullptr;
+                lb_destroy(c);
+                return LB_E_NOMEM;
+            }
+            if (cudaMemset(c->chain_flag, 0, sizeof(unsigned) * (size_t)tx * ty) != cudaSuccess) {
+                cudaGetLastError();
+                lb_destroy(c);
+                return LB_E_CUDA;
+            }
+            const int wave_rows = (per_sm * sms + tx - 1) / tx;
+            c->chain_rows = wave_rows + 3 < ty ? wave_rows + 3 : ty;
+            c->chain_step = 1u;
+        } else {
             cudaGetLastError();
-            lb_destroy(c);
-            return LB_E_NOMEM;
         }
-        const int wave_rows = (per_sm * sms + tx - 1) / tx;
-        c->chain_rows = wave_rows + 3 < ty ? wave_rows + 3 : ty;
-        c->chain_step = 1u;
     }
     *out = c;
     return LB_OK;
