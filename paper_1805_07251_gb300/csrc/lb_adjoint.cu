@@ -223,14 +223,19 @@ lb_status lb_rollout_forward(lb_ctx *c, int64_t nsteps, int32_t ckpt_every) {
         c->ckpt.push_back(p);
     }
     c->ckpt_every = ckpt_every;
-    for (int64_t t = 0; t < nsteps; ++t) {
+    // one lb_step call per segment between checkpoints (chained where the configuration
+    // chains: the same bits as single steps, so the backward recompute repeats them)
+    for (int64_t t = 0; t < nsteps;) {
         if (t % ckpt_every == 0) {
             if (cudaMemcpyAsync(c->ckpt[t / ckpt_every], c->f[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream) !=
                 cudaSuccess)
                 return rfail(c, LB_E_CUDA, "checkpoint copy");
         }
-        lb_status s = lb_step(c, 1);
+        int64_t seg = ckpt_every - t % ckpt_every;
+        if (seg > nsteps - t) seg = nsteps - t;
+        lb_status s = lb_step(c, seg);
         if (s != LB_OK) return s;
+        t += seg;
     }
     c->rollout_steps = nsteps;
     return LB_OK;
