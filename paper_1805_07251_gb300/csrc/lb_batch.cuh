@@ -17,11 +17,13 @@
 
 namespace lbvdw {
 
-// One tile of the flat work list: its run, origin, the run's lattice size and the run's
-// element offset in the pools (what the tile needs before its parameter block arrives).
+// One tile of the flat work list: its run, origin, the run's lattice size, element offset
+// in the pools and reference densities (what the tile needs before its parameter block
+// arrives).
 struct BatchTile {
     int run, x0, y0, nx, ny, pad;
     size_t off;
+    float rho_ref[4];
 };
 
 // Copy a run's parameter block into shared memory (the single-run kernels get theirs as a
@@ -42,18 +44,19 @@ __global__ void __launch_bounds__(TX *TY, MinBlocks<S, N, TX * TY, PairPath<N, S
     const int tid = threadIdx.x + TX * threadIdx.y;
     __shared__ __align__(16) DevParams s_p;
     if constexpr (PairPath<N, S, R, MU>::value) {
-        // the parameter block is requested here and stored once the tile's populations are
-        // requested too, so the two global round trips overlap
+        // the parameter block is requested here and stored at the end of the densities
+        // phase, which needs only the tile entry: the two global round trips overlap, and
+        // the step's first barrier publishes the block
         constexpr int W = (int)(sizeof(DevParams) / 8);
         static_assert(sizeof(DevParams) % 8 == 0 && W <= TX * TY, "one 8-byte word of DevParams per thread");
         int2 w = make_int2(0, 0);
         if (tid < W) w = reinterpret_cast<const int2 *>(runs + t.run)[tid];
         auto hook = [&]() {
             if (tid < W) reinterpret_cast<int2 *>(&s_p)[tid] = w;
-            __syncthreads();
         };
-        step_tile_pair<2, N / 2, TX, TY, FORCE, MU>(pool_in + t.off, pool_out + t.off, s_p, t.x0, t.y0,
-                                                    TileGeo{t.nx, t.ny, tbl}, hook);
+        step_tile_pair<2, N / 2, TX, TY, FORCE, MU>(
+            pool_in + t.off, pool_out + t.off, s_p, t.x0, t.y0,
+            TileGeo{t.nx, t.ny, tbl, {t.rho_ref[0], t.rho_ref[1], t.rho_ref[2], t.rho_ref[3]}}, hook);
     } else {
         stage_params(s_p, runs + t.run, tid, TX * TY);
         __syncthreads();

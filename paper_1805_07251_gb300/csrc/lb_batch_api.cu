@@ -69,19 +69,36 @@ void clear_graphs(lb_batch *b) {
     b->graphs.clear();
 }
 
-cudaError_t build_tiles(lb_batch *b) {
+// The tile list of the D2Q9 runs (host copy), with each run's current reference densities.
+std::vector<BatchTile> tile_list(const lb_batch *b) {
     std::vector<BatchTile> t;
     for (int r : b->d2) {
         const lb_run_desc &d = b->desc[r];
+        const DevParams &P = b->hparams[r];
         for (int y0 = 0; y0 < d.ny; y0 += b->tile_y)
-            for (int x0 = 0; x0 < d.nx; x0 += b->tile_x) t.push_back({r, x0, y0, d.nx, d.ny, 0, b->offsets[r]});
+            for (int x0 = 0; x0 < d.nx; x0 += b->tile_x)
+                t.push_back({r, x0, y0, d.nx, d.ny, 0, b->offsets[r],
+                             {P.rho_ref_f[0], P.rho_ref_f[1], P.rho_ref_f[2], P.rho_ref_f[3]}});
     }
+    return t;
+}
+
+cudaError_t build_tiles(lb_batch *b) {
+    std::vector<BatchTile> t = tile_list(b);
     cudaFree(b->d_tiles);
     b->d_tiles = nullptr;
     b->ntiles = (int)t.size();
     if (t.empty()) return cudaSuccess;
     cudaError_t e = cudaMalloc(&b->d_tiles, sizeof(BatchTile) * t.size());
     if (e != cudaSuccess) return e;
+    return cudaMemcpy(b->d_tiles, t.data(), sizeof(BatchTile) * t.size(), cudaMemcpyHostToDevice);
+}
+
+// Rewrite the tile list in place (same device array, so captured graphs stay valid) after
+// the runs' reference densities changed.
+cudaError_t refresh_tiles(lb_batch *b) {
+    if (b->ntiles == 0) return cudaSuccess;
+    std::vector<BatchTile> t = tile_list(b);
     return cudaMemcpy(b->d_tiles, t.data(), sizeof(BatchTile) * t.size(), cudaMemcpyHostToDevice);
 }
 
@@ -390,6 +407,7 @@ lb_status lb_batch_init(lb_batch *b, const double *rho_all) {
         pos += (size_t)N * n;
     }
     LB_BCUDA(b, cudaMemcpy(b->d_params, b->hparams.data(), sizeof(DevParams) * b->nruns, cudaMemcpyHostToDevice));
+    LB_BCUDA(b, refresh_tiles(b));
     LB_BCUDA(b, cudaMemset(b->d_err, 0, sizeof(unsigned) * b->nruns));
     b->cur = 0;
     b->steps = 0;

@@ -916,16 +916,18 @@ __device__ __forceinline__ float ld_pop(const float *p) {
     else return *p;
 }
 
-// What a tile step needs before it reads its parameter block: the lattice size and the
-// log tables.  The single-run kernels take them from the parameter block itself (a kernel
-// parameter); the batched tile kernel from its tile entry, so that its populations are
-// requested while the run's parameter block is still on its way into shared memory.
+// What a tile step needs before it reads its parameter block (its densities phase): the
+// lattice size, the log tables and the components' reference densities.  The single-run
+// kernels take them from the parameter block itself (a kernel parameter); the batched tile
+// kernel from its tile entry, so that its populations are requested while the run's
+// parameter block is still on its way into shared memory.
 struct TileGeo {
     int nx, ny;
     const LogTables *tbl;
+    float rho_ref[4];
 };
 
-// The default hook of step_tile_pair: nothing between the node's loads and their use.
+// The default hook of step_tile_pair: nothing before the first barrier.
 struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
@@ -935,8 +937,8 @@ struct NoHook {
 // forces, populations) and is computed by the packed FP32x2 instructions; shared memory
 // holds the pairs interleaved, so one 8-byte (16-byte for double-float mu) access moves
 // both components.  Same arithmetic as the general step_tile below, bitwise.
-// `hook` runs on every thread once the node's own populations are requested and before any
-// field of P but those in `geo` is read (the batched kernel completes its parameter block
+// The densities phase reads only `geo`; `hook` runs on every thread at its end, before the
+// first barrier, after which P is read (the batched kernel completes its parameter block
 // in shared memory there).
 template <int LAT, int NP, int TX, int TY, int FORCE, int MU, int LD = 0, class Hook = NoHook>
 __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, float *__restrict__ fout,
@@ -969,7 +971,7 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
     const size_t plane = (size_t)nx * (size_t)ny;
     const size_t cq = (size_t)Q * plane;  // component stride
     const bool small = nx <= TX + 1 || (LAT == 2 && ny <= TY + 1);
-    auto rref = [&](int q) { return make_float2(P.rho_ref_f[2 * q], P.rho_ref_f[2 * q + 1]); };
+    auto rref = [&](int q) { return make_float2(geo.rho_ref[2 * q], geo.rho_ref[2 * q + 1]); };
 
     // One pair: 32-bit element offsets within a component's Q planes (Q nx ny < 2^32 for
     // FP32 storage, checked when the context is created) from per-component base pointers,
@@ -992,7 +994,6 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
             float2 gv[Q], acc;
 #pragma unroll
             for (int i = 0; i < Q; ++i) gv[i] = make_float2(ld(2 * q, i, off), ld(2 * q + 1, i, off));
-            if (q == 0) hook();
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 if constexpr (STAGE) s_g[i][tid] = gv[i];
@@ -1017,6 +1018,7 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
             s_rho[q][ey * EX + ex] = v_add(rref(q), acc);
         }
     }
+    hook();
     __syncthreads();
 
     // ---- phase 2: phi on tile + 1 ring --------------------------------------------
@@ -1146,7 +1148,9 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
 template <int LAT, int NP, int TX, int TY, int FORCE, int MU, int LD = 0>
 __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, float *__restrict__ fout,
                                                const DevParams &P, int x0, int y0) {
-    step_tile_pair<LAT, NP, TX, TY, FORCE, MU, LD>(fin, fout, P, x0, y0, TileGeo{P.nx, P.ny, P.tbl}, NoHook());
+    step_tile_pair<LAT, NP, TX, TY, FORCE, MU, LD>(
+        fin, fout, P, x0, y0,
+        TileGeo{P.nx, P.ny, P.tbl, {P.rho_ref_f[0], P.rho_ref_f[1], P.rho_ref_f[2], P.rho_ref_f[3]}}, NoHook());
 }
 
 // The fused step on one TX x TY tile with origin (x0, y0) of the lattice described by P.
