@@ -82,11 +82,11 @@ def parse(argv=None):
 # it and is reported as null once they change.
 KERNEL_SOURCES = ("lb_kernels.cuh", "lb_chain.cuh", "lb_lane.cuh", "lb_mu.cuh", "lb_tu.cuh", "lb_launch.cuh",
                   "lb_d2q9_df.cu")
-TRAFFIC = {"fp32_dfmu": {"digest": "8f35cfb6c8d24a2ccc5aa6dc421a7bb7d516a82cb4fd684dd0dae61e1401a3a9",
-                         "bytes": 109129728, "warp_instructions": 29557472, "issue_active": 0.589,
-                         "fma_pipe_active": 0.521,
-                         "stalls_per_issue": {"barrier": 2.91, "long_scoreboard": 2.66, "not_selected": 2.46,
-                                              "math_pipe_throttle": 2.13, "wait": 1.24},
+TRAFFIC = {"fp32_dfmu": {"digest": "86ef663985505818c509fa6d3f43d9dcc73efe8364c65302f1517af9a47ee3d1",
+                         "bytes": 109316864, "warp_instructions": 29557472, "issue_active": 0.590,
+                         "fma_pipe_active": 0.518,
+                         "stalls_per_issue": {"barrier": 2.89, "long_scoreboard": 2.68, "not_selected": 2.48,
+                                              "math_pipe_throttle": 2.12, "wait": 1.24},
                          "profile": "profiles/lb_chain_kernel_fp32_dfmu_c2_1024.md"}}
 # instruction issue peak of the GPU: 152 SMs x 4 schedulers x 2.07 GHz (one warp instruction
 # per scheduler per cycle)
