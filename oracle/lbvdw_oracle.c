@@ -52,8 +52,11 @@
  * "nid" force is pinned by its exact zero for an ideal mixture at gamma kT = theta
  * and by its second-order agreement with the "log" force under refinement; the
  * pivoted N-component friction solve by the closed-form uniform relaxation
- * u_{n+1} = (D + L/2)^-1 (D - L/2) u_n.  Lambda's role in nonlinear dynamics
- * (coarsening, interface motion) beyond these is "parity unpinned".
+ * u_{n+1} = (D + L/2)^-1 (D - L/2) u_n.  Lambda in nonlinear dynamics is pinned
+ * by the interdiffusion of an ideal mixture, which the Maxwell-Stefan balance of
+ * Sec. IV makes linear diffusion at any composition: a wave from x = 0.1 to 0.9
+ * decays at the small-amplitude rate.  Coarsening and interface motion, which
+ * have no closed form, are "parity unpinned".
  */
 #include <math.h>
 #include <stdlib.h>

@@ -536,6 +536,50 @@ def test_interdiffusion_follows_maxwell_stefan_fick_law(lam):
     assert abs(rate / predicted - 1) < 0.01
 
 
+@pytest.mark.parametrize("force", ["nid", "log"])
+@pytest.mark.parametrize("lam", [0.5, 2.0])
+def test_ideal_mixture_interdiffusion_is_linear_at_large_amplitude(force, lam):
+    # lambda in nonlinear dynamics (Sec. IV, Eq. MaxwellStefan): for an ideal mixture
+    # (a = kappa = 0, equal b, so eta depends on the total density only) at uniform total
+    # density rho, the Maxwell-Stefan balance lambda rho^A rho^B (u^A - u^B) / rho =
+    # -gamma (rho^B rho^A D mu^A - rho^A rho^B D mu^B) / rho gives the flux
+    # J^A = -(gamma kT / lambda) D rho^A: linear diffusion whatever the composition.
+    # (With the "nid" force at gamma kT = theta the mean-field force vanishes and the
+    # lattice's own pressure theta rho^c drives it, so D = theta / lambda.)  A composition
+    # wave from x = 0.1 to 0.9 therefore decays at the small-amplitude rate, with no even
+    # harmonics (the dynamics are odd under A <-> B); the friction's composition weight
+    # rho^A rho^B / (rho^A + rho^B) and the implicit u-hat must cancel the driving force's
+    # composition dependence exactly, which a linearised check cannot see.
+    nx, rho, kT = 256, 1.6, 0.5
+    gam = THETA / kT if force == "nid" else 0.6
+    k = 2 * np.pi / nx
+    x = np.arange(nx)
+    rates, last = {}, {}
+    for A in (0.005, 0.4):
+        L = lat("D1Q3", nx, 1, 2, kT=kT, gamma=gam, a=np.zeros((2, 2)), kappa=0.0, b=[0.2, 0.2],
+                lam=[[0, lam], [lam, 0]], force_method=1 if force == "nid" else 0)
+        xa = 0.5 + A * np.cos(k * x)
+        f = L.equilibrium(np.stack([rho * xa, rho * (1 - xa)]).reshape(L.rshape()))
+        ts, a1, a2, a3 = [], [], [], []
+        for t in range(1, 41):
+            f = L.run(f, 250)
+            r, _ = L.moments(f)
+            d = 0.5 * (r[0, 0] - r[1, 0])
+            ts.append(250 * t)
+            a1.append(abs(np.mean(d * np.exp(-1j * k * x))))
+            a2.append(abs(np.mean(d * np.exp(-2j * k * x))))
+            a3.append(abs(np.mean(d * np.exp(-3j * k * x))))
+        a1 = np.array(a1)
+        rates[A] = -np.polyfit(ts[5:], np.log(a1[5:]), 1)[0]
+        last[A] = a1[-1] / (rho * A)
+        assert max(np.array(a2) / a1) < 1e-9
+        assert max(np.array(a3) / a1) < 1e-3
+    predicted = (THETA if force == "nid" else gam * kT) * k * k / lam
+    assert abs(rates[0.005] / predicted - 1) < 0.005
+    assert abs(rates[0.4] / rates[0.005] - 1) < 1e-5
+    assert abs(last[0.4] / last[0.005] - 1) < 1e-4
+
+
 # ------------------------------------------------------------ MRT collision (D2Q9)
 
 def test_mrt_with_equal_relaxation_times_is_bgk():
