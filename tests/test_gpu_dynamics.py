@@ -1,6 +1,8 @@
 """GPU tests of the method's dynamics beyond parity of single steps: linear interdiffusion
 of a composition wave at the Maxwell-Stefan / Fick rate of Sec. IV (Eq. MaxwellStefan and
-its Fickian limit), on the GPU against the rate and against the FP64 oracle's trajectory."""
+its Fickian limit), on the GPU against the rate and against the FP64 oracle's trajectory;
+the large-amplitude interdiffusion of an ideal mixture, linear at any composition; the
+moment-space collision against the oracle."""
 import numpy as np
 import pytest
 
@@ -67,6 +69,56 @@ def test_gpu_interdiffusion_follows_maxwell_stefan_fick_law(gpu_lib, parity_boun
             ro, _ = L.moments(f)
             worst = max(worst, abs(_amplitude(ro, k, x) - amps[t - 1]) / amps[t - 1])
         parity_bound("amplitude vs oracle (rel.)", worst, 1e-9)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_dfmu"])
+@pytest.mark.parametrize("force", ["nid", "log"])
+def test_gpu_ideal_mixture_interdiffusion_is_linear_at_large_amplitude(gpu_lib, parity_bound, force, precision):
+    # Sec. IV (Eq. MaxwellStefan): an ideal mixture (a = kappa = 0, equal b) at uniform
+    # total density interdiffuses by linear diffusion at any composition, flux
+    # -(gamma kT / lambda) D rho^A ("nid" at gamma kT = theta: theta / lambda).  A
+    # composition wave from x = 0.1 to 0.9 must decay at the small-amplitude rate and at
+    # the Fick rate, as it does in the oracle, and in FP64 follow the oracle's amplitudes.
+    from paper_1805_07251_gb300 import Simulation
+
+    nx, rho, kT, lam = 256, 1.6, 0.5, 2.0
+    theta = 1.0 / 3.0
+    gam = theta / kT if force == "nid" else 0.6
+    k = 2 * np.pi / nx
+    x = np.arange(nx)
+    kw = dict(lattice="D1Q3", nx=nx, ny=1, ncomp=2, tau=1.0, kT=kT, gamma_mu=gam, a=np.zeros((2, 2)),
+              kappa=np.zeros((2, 2)), lam=np.array([[0.0, lam], [lam, 0.0]]), b=np.array([0.2, 0.2]))
+    rates, hist = {}, {}
+    for A in (0.005, 0.4):
+        xa = 0.5 + A * np.cos(k * x)[None, :]
+        r0 = np.stack([rho * xa, rho * (1 - xa)])
+        sim = Simulation(precision=precision, force=force, **kw)
+        sim.init(r0)
+        ts, amps = [], []
+        for t in range(1, 41):
+            sim.step(250)
+            r, _ = sim.moments()
+            ts.append(250 * t)
+            amps.append(_amplitude(r, k, x))
+        sim.close()
+        rates[A] = -np.polyfit(ts[5:], np.log(amps[5:]), 1)[0]
+        hist[A] = (r0, amps)
+    predicted = (theta if force == "nid" else gam * kT) * k * k / lam
+    parity_bound("small-amplitude rate / Fick rate - 1", abs(rates[0.005] / predicted - 1), 0.005)
+    # FP32 storage: the small wave's amplitude (8e-3) sits ~1e5 above the rounding floor
+    parity_bound("large / small amplitude rate - 1", abs(rates[0.4] / rates[0.005] - 1),
+                 5e-5 if precision == "fp64" else 2e-4)
+    if precision == "fp64":
+        r0, amps = hist[0.4]
+        L = oracle.Lattice("D1Q3", nx, 1, 2, 1.0, kT, gam, kw["a"], kw["kappa"], kw["lam"], kw["b"],
+                           force_method=1 if force == "nid" else 0)
+        f = L.equilibrium(r0)
+        worst = 0.0
+        for t in range(1, 41):
+            f = L.run(f, 250)
+            ro, _ = L.moments(f)
+            worst = max(worst, abs(_amplitude(ro, k, x) - amps[t - 1]) / amps[t - 1])
+        parity_bound("large-amplitude history vs oracle (rel.)", worst, 1e-9)
 
 
 # ------------------------------------------------------------ moment-space collision

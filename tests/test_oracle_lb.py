@@ -573,10 +573,13 @@ def test_ideal_mixture_interdiffusion_is_linear_at_large_amplitude(force, lam):
         rates[A] = -np.polyfit(ts[5:], np.log(a1[5:]), 1)[0]
         last[A] = a1[-1] / (rho * A)
         assert max(np.array(a2) / a1) < 1e-9
-        assert max(np.array(a3) / a1) < 1e-3
+        # measured up to 1.0e-4 (the lattice's own weak nonlinearity); composition-dependent
+        # mistakes in the friction or the force give 1e-3 to 1e-1
+        assert max(np.array(a3) / a1) < 5e-4
     predicted = (THETA if force == "nid" else gam * kT) * k * k / lam
     assert abs(rates[0.005] / predicted - 1) < 0.005
-    assert abs(rates[0.4] / rates[0.005] - 1) < 1e-5
+    # measured up to 7.1e-6 ("log", lambda = 2); those mistakes move it by 1.7e-4 to 7e-2
+    assert abs(rates[0.4] / rates[0.005] - 1) < 5e-5
     assert abs(last[0.4] / last[0.005] - 1) < 1e-4
 
 
