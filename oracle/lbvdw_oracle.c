@@ -55,8 +55,10 @@
  * u_{n+1} = (D + L/2)^-1 (D - L/2) u_n.  Lambda in nonlinear dynamics is pinned
  * by the interdiffusion of an ideal mixture, which the Maxwell-Stefan balance of
  * Sec. IV makes linear diffusion at any composition: a wave from x = 0.1 to 0.9
- * decays at the small-amplitude rate.  Coarsening and interface motion, which
- * have no closed form, are "parity unpinned".
+ * decays at the small-amplitude rate.  No function here is without a pin; what no
+ * closed form covers is the transient of coarsening and interface motion, whose
+ * end states are pinned (coexistence on the common tangent, the Maxwell
+ * construction) but whose rates are not.
  */
 #include <math.h>
 #include <stdlib.h>
