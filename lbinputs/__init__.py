@@ -149,6 +149,21 @@ def fields(name, nx=None, ny=None):
     raise KeyError(name)
 
 
+def fields_on_device(name, nx, ny, device, seed_value):
+    """The recipe of workload ``name`` (its mean densities, Gaussian noise of sigma 1e-2) on a
+    lattice too large for host-side generation: a torch CUDA tensor rho [c][y][x] in FP64
+    from torch's seeded generator (a different stream from ``fields``)."""
+    import torch
+
+    p = base_params(name)
+    mean = torch.tensor(p["rho_total"] * p["x"], dtype=torch.float64, device=device)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed_value))
+    rho = torch.randn((p["ncomp"], ny, nx), generator=g, dtype=torch.float64, device=device)
+    rho.mul_(1e-2).add_(mean[:, None, None])
+    return rho
+
+
 def uniform_noise_fields(ncomp, ny, nx, mean, sigma, seed_value):
     """Uniform means plus Gaussian noise (used by small parity cases)."""
     r = np.random.default_rng(seed_value)

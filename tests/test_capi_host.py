@@ -163,3 +163,35 @@ def test_warp_specialised_kernel_is_validated_without_cuda(lib):
         for k, v in change.items():
             setattr(p, k, v)
         assert lib.lb_create(ctypes.byref(p), ctypes.byref(out)) == capi.LB_E_INVALID, change
+
+
+def test_lattice_size_limits_are_validated_without_cuda(lib):
+    # FP32 storage addresses a component's Q planes with 32-bit element offsets, so
+    # Q nx ny must stay below 2^32; every precision needs nx ny <= 2^31.  A size at the
+    # limit fails validation (LB_E_INVALID) before any CUDA call; one node row below it
+    # passes validation (on a host without a GPU it then fails at the first CUDA call; where
+    # a GPU has the memory the context is created, and destroyed again here).
+    from paper_1805_07251_gb300 import capi
+
+    out = ctypes.c_void_p()
+
+    def create(precision, lattice, nx, ny):
+        p = capi.lb_default_params()
+        p.b[0] = p.b[1] = 0.3
+        p.precision, p.lattice, p.nx, p.ny = precision, lattice, nx, ny
+        st = lib.lb_create(ctypes.byref(p), ctypes.byref(out))
+        if st == capi.LB_OK:
+            lib.lb_destroy(out)
+        return st
+
+    nx = 32768  # 9 nx ny = 2^32 at ny = 2^32 / (9 nx), which is not an integer
+    ny_lim = -(-(1 << 32) // (9 * nx))  # smallest ny with 9 nx ny >= 2^32
+    assert 9 * nx * ny_lim >= 1 << 32 > 9 * nx * (ny_lim - 1)
+    for prec in (capi.LB_FP32_DFMU, capi.LB_FP32_MIXED, capi.LB_FP32):
+        assert create(prec, capi.LB_D2Q9, nx, ny_lim) == capi.LB_E_INVALID
+    assert create(capi.LB_FP32_DFMU, capi.LB_D2Q9, nx, ny_lim - 1) != capi.LB_E_INVALID
+    nx3 = -(-(1 << 32) // 3)  # D1Q3: 3 nx >= 2^32
+    assert create(capi.LB_FP32_DFMU, capi.LB_D1Q3, nx3, 1) == capi.LB_E_INVALID
+    # FP64: 64-bit offsets, nx ny <= 2^31 only (2^31 FP64 nodes exceed any GPU's memory)
+    assert create(capi.LB_FP64, capi.LB_D2Q9, 1 << 16, (1 << 15) + 1) == capi.LB_E_INVALID
+    assert create(capi.LB_FP64, capi.LB_D2Q9, 1 << 16, 1 << 15) not in (capi.LB_E_INVALID, capi.LB_OK)
