@@ -665,3 +665,30 @@ def test_ws_kernel_full_size_matches_tiles(gpu_lib):
     p = lbinputs.base_params("c2")
     (r_t, j_t), (r_w, j_w) = ws_case(p, p["nx"], p["ny"], "fp32_dfmu", steps=20)
     assert np.array_equal(r_t, r_w) and np.array_equal(j_t, j_w)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_dfmu"])
+@pytest.mark.parametrize("lattice,nx,ny", [("D2Q9", 2, 2), ("D2Q9", 3, 2), ("D2Q9", 2, 5), ("D2Q9", 5, 3),
+                                           ("D2Q9", 7, 9), ("D2Q9", 33, 3), ("D2Q9", 31, 17),
+                                           ("D1Q3", 2, 1), ("D1Q3", 3, 1), ("D1Q3", 5, 1), ("D1Q3", 127, 1)])
+def test_degenerate_lattices_match_oracle(gpu_lib, parity_bound, precision, lattice, nx, ny):
+    # lattices narrower than a tile and its ring (the periodic wrap reaches a node more than
+    # once, down to 2 nodes), one tile with a ragged edge, and lb_step(0): the one-phase
+    # config-2 mixture, so 50 steps agree to the FP64 bar, or to FP32 rounding
+    p = lbinputs.base_params("c2")
+    kT = 1.1 * lbinputs.one_fluid_critical_kT(p["a"], p["b"], p["x"])
+    sim, orc = make_pair(p, precision=precision, nx=nx, ny=ny, kT=kT, lattice=lattice)
+    rho = lbinputs.uniform_noise_fields(2, ny, nx, 1.2 * p["x"], 1e-2, 3000 + nx * 100 + ny)
+    sim.init(rho)
+    r0, j0 = sim.moments()
+    sim.step(0)
+    r1, j1 = sim.moments()
+    assert np.array_equal(r0, r1) and np.array_equal(j0, j1)
+    sim.step(50)
+    r_g, j_g = sim.moments()
+    f = orc.run(orc.equilibrium(rho), 50)
+    r_o, j_o = orc.moments(f)
+    bound = 1e-12 if precision == "fp64" else 1e-5
+    parity_bound(f"{lattice} {nx}x{ny}: rho rel. max, 50 steps", rel_err(r_g, r_o), bound)
+    parity_bound(f"{lattice} {nx}x{ny}: j / max rho", np.max(np.abs(j_g - j_o)) / np.max(np.abs(r_o)), bound)
+    sim.close()
