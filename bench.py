@@ -88,6 +88,12 @@ TRAFFIC = {"fp32_dfmu": {"digest": "86ef663985505818c509fa6d3f43d9dcc73efe8364c6
                          "stalls_per_issue": {"barrier": 2.89, "long_scoreboard": 2.68, "not_selected": 2.48,
                                               "math_pipe_throttle": 2.12, "wait": 1.24},
                          "profile": "profiles/lb_chain_kernel_fp32_dfmu_c2_1024.md"}}
+# FP64-pipe utilisation of the two FP64-bound paths (sm__pipe_fp64_cycles_active of one
+# launch, the profile named beside it), valid for the kernel sources of the same digest
+FP64_PIPE = {"digest": "86ef663985505818c509fa6d3f43d9dcc73efe8364c65302f1517af9a47ee3d1",
+             "fp32_mixed": 0.840, "fp64": 0.851, "profile": "profiles/lb_step_kernel_fp64_c2_1024.md"}
+# nominal HBM3e bandwidth of the GPU (GB/s), reported beside the measured copy peak
+HBM_NOMINAL_GBS = 7900.0
 # instruction issue peak of the GPU: 152 SMs x 4 schedulers x 2.07 GHz (one warp instruction
 # per scheduler per cycle)
 ISSUE_PEAK = 152 * 4 * 2.07e9
@@ -807,6 +813,7 @@ def main():
                                                                                       "lb_step_kernel"),
                          head["kernel"].split()[1], HEAD),
                      "alg_bytes_per_launch": head["alg_bytes"],
+                     "frac_of_nominal": head["achieved"] / HBM_NOMINAL_GBS, "nominal_gbs": HBM_NOMINAL_GBS,
                      "duration": "K launches between two CUDA events / K",
                      "limiter": limiter_of(HEAD, head["alg_bytes"], peak_gbs)},
         "gpu_launches": head["launches"],
@@ -844,6 +851,9 @@ def main():
                       "roofline_hbm": {"achieved": rr["achieved"], "peak": peak_gbs, "unit": "GB/s",
                                        "frac": rr["achieved"] / peak_gbs},
                       "flushed": rr["flushed"]}
+        if key in FP64_PIPE and FP64_PIPE["digest"] == kernel_digest():
+            line[name]["fp64_pipe_active"] = FP64_PIPE[key]
+            line[name]["fp64_pipe_profile"] = FP64_PIPE["profile"]
         line["gpu_launches"] += rr["launches"]
     if clocks:
         line["clocks"] = clocks
