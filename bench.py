@@ -82,11 +82,11 @@ def parse(argv=None):
 # it and is reported as null once they change.
 KERNEL_SOURCES = ("lb_kernels.cuh", "lb_chain.cuh", "lb_lane.cuh", "lb_mu.cuh", "lb_tu.cuh", "lb_launch.cuh",
                   "lb_d2q9_df.cu")
-TRAFFIC = {"fp32_dfmu": {"digest": "86ef663985505818c509fa6d3f43d9dcc73efe8364c65302f1517af9a47ee3d1",
-                         "bytes": 109316864, "warp_instructions": 29557472, "issue_active": 0.590,
-                         "fma_pipe_active": 0.518,
-                         "stalls_per_issue": {"barrier": 2.89, "long_scoreboard": 2.68, "not_selected": 2.48,
-                                              "math_pipe_throttle": 2.12, "wait": 1.24},
+TRAFFIC = {"fp32_dfmu": {"digest": "7beb09f974cde77630c9b30434b768a5bf723b374759841067535a37725fe51c",
+                         "bytes": 76000512 + 17210880, "warp_instructions": 29754080, "issue_active": 0.595,
+                         "fma_pipe_active": 0.520,
+                         "stalls_per_issue": {"barrier": 2.90, "long_scoreboard": 2.49, "not_selected": 2.52,
+                                              "math_pipe_throttle": 2.14, "wait": 1.23},
                          "profile": "profiles/lb_chain_kernel_fp32_dfmu_c2_1024.md"}}
 # FP64-pipe utilisation of the two FP64-bound paths (sm__pipe_fp64_cycles_active of one
 # launch, the profile named beside it), valid for the kernel sources of the same digest
@@ -738,6 +738,7 @@ def main():
         results[precision] = dict(
             value=job_throughput(world, N * nodes * args.steps, job_ms * 1e-3), ms=ms, launches=launches,
             alg_bytes=alg_bytes, achieved=alg_bytes / (ms * 1e-3) / 1e9, chained=sim.chain_rows > 0,
+            evict_first=sim.chain_evict_first,
             kernel="%s %dx%d" % (kind, tile[0], tile[1]),
             flushed={"value": job_throughput(world, N * nodes, fl_ms * 1e-3), "unit": UNIT, "ms_per_step": fl_ms,
                      "achieved_gbs": alg_bytes / (fl_ms * 1e-3) / 1e9,
@@ -798,7 +799,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPES[HEAD], "data": "synthetic",
         "config": {"workload": "D2Q9, 2 components, 1024x1024 periodic, spinodal mixture (c2), " + HEAD,
-                   "nodes": nodes, "ncomp": N, "kernel": head["kernel"] + (", chained" if head["chained"] else ""),
+                   "nodes": nodes, "ncomp": N, "kernel": head["kernel"] + (", chained" if head["chained"] else "")
+                   + (", input evict-first in the L2" if head["evict_first"] else ""),
                    "l2": "no flush: the job's state (two population buffers, %.0f MB) is larger than the 129 MB "
                          "L2; the K timed steps run back to back in one lb_step call between two CUDA events. "
                          "One launch per step with a 256 MB L2 flush before each: 'flushed'"

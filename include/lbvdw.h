@@ -339,6 +339,14 @@ int64_t lb_launch_count(const lb_ctx *ctx);
  * the configuration is not chained, -1 for a NULL context. */
 int32_t lb_chain_rows(const lb_ctx *ctx);
 
+/* Whether the chained steps of this context load their input populations with an
+ * evict-first L2 cache policy: 1 where one population buffer (N Q nx ny stored values) takes
+ * at most 60 % of the device's L2, so that each step's output stays resident in the L2 for
+ * the next step's reads; 0 otherwise or when not chained; -1 for a NULL context.  A cache
+ * policy changes no result.  (Implementation choice of this library; the paper has no
+ * counterpart.) */
+int32_t lb_chain_evict_first(const lb_ctx *ctx);
+
 /* Copy the context's parameters as resolved by lb_create (kernel organisation and
  * tile chosen for LB_KERNEL_AUTO and tile 0 x 0) into *out.  Errors: LB_E_INVALID
  * (NULL argument). */

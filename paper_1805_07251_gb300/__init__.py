@@ -134,6 +134,11 @@ class Simulation:
         return capi.lb_chain_rows(self.ctx)
 
     @property
+    def chain_evict_first(self):
+        """Whether the chained steps mark their input evict-first in the L2 (lb_chain_evict_first)."""
+        return bool(capi.lb_chain_evict_first(self.ctx))
+
+    @property
     def kernel(self):
         """Organisation of the step kernel chosen by lb_create: ("tiles" or "strips", tile)."""
         p = capi.lb_get_params(self.ctx)

@@ -100,6 +100,7 @@ def load():
         "lb_step_count": (ctypes.c_int64, [C]),
         "lb_launch_count": (ctypes.c_int64, [C]),
         "lb_chain_rows": (ctypes.c_int32, [C]),
+        "lb_chain_evict_first": (ctypes.c_int32, [C]),
         "lb_get_params": (ctypes.c_int, [C, ctypes.POINTER(lb_params)]),
         "lb_destroy": (ctypes.c_int, [C]),
         "lb_status_str": (ctypes.c_char_p, [ctypes.c_int]),
@@ -222,6 +223,10 @@ def lb_launch_count(ctx):
 
 def lb_chain_rows(ctx):
     return int(load().lb_chain_rows(ctx))
+
+
+def lb_chain_evict_first(ctx):
+    return int(load().lb_chain_evict_first(ctx))
 
 
 def lb_get_params(ctx):

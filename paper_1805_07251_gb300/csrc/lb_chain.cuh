@@ -39,6 +39,7 @@ struct ChainArgs {
     int release_rows;         // CTA rows of this step that set flags (0: no next step)
     int roff;                 // row rotation: CTA row b takes tile row (b + roff) mod rows
     unsigned long long wait_ns;  // bound of one flag wait
+    int evict_first;          // population loads marked evict-first in the L2 (lb_chain_kernel<.., true>)
 };
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
@@ -74,8 +75,11 @@ __device__ __forceinline__ bool wait_flag(const unsigned *flag, int idx, unsigne
     return true;
 }
 
-// One chained step: D2Q9, N = 2 FP32 components in one lane pair, 32 x 8 tiles.
-template <int FORCE, int MU>
+// One chained step: D2Q9, N = 2 FP32 components in one lane pair, 32 x 8 tiles.  EF: the
+// population loads carry an evict-first L2 policy (chosen by the host where one population
+// buffer fits in the L2 with room to spare, so that the step's output stays resident for the
+// next step); the results are the same bits either way.
+template <int FORCE, int MU, bool EF = false>
 __global__ void __launch_bounds__(256, 5)
     lb_chain_kernel(const float *__restrict__ fin, float *__restrict__ fout, DevParams P, ChainArgs ca) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -96,7 +100,7 @@ __global__ void __launch_bounds__(256, 5)
         }
     }
     // the loads bypass L1: the previous grid may still write this grid's input
-    step_tile_pair<2, 1, 32, 8, FORCE, MU, 1>(fin, fout, P, blockIdx.x * 32, r * 8);
+    step_tile_pair<2, 1, 32, 8, FORCE, MU, 1, EF>(fin, fout, P, blockIdx.x * 32, r * 8);
     if ((int)blockIdx.y < ca.release_rows) {
         // every thread's stores of the tile come before the flag: the barrier orders them
         // before thread 0's release, whose fence is cumulative over what it orders

@@ -34,6 +34,7 @@ struct lb_ctx {
     unsigned chain_step = 0;
     int chain_roff = 0;
     int chain_rows = 0;
+    int chain_evict_first = 0;  // chained steps load their input with an evict-first L2 policy
     int64_t steps = 0, launches = 0;
     bool has_state = false, poisoned = false;
     std::string msg;

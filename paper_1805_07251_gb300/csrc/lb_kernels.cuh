@@ -916,6 +916,23 @@ __device__ __forceinline__ float ld_pop(const float *p) {
     else return *p;
 }
 
+// An L2 cache policy that marks the lines it touches first for eviction (PTX createpolicy)
+__device__ __forceinline__ unsigned long long l2_evict_first_policy() {
+    unsigned long long q;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(q));
+    return q;
+}
+
+// The L2-only load of a chained step with an L2 cache policy.  A step reads its input once
+// (and its ring again within the step) and never after, so where one population buffer
+// fits in the L2 with room to spare, marking the input evict-first keeps the output just
+// written resident for the next step's reads.
+__device__ __forceinline__ float ld_pop_policy(const float *p, unsigned long long pol) {
+    float v;
+    asm volatile("ld.global.cg.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
 // What a tile step needs before it reads its parameter block (its densities phase): the
 // lattice size, the log tables and the components' reference densities.  The single-run
 // kernels take them from the parameter block itself (a kernel parameter); the batched tile
@@ -925,6 +942,7 @@ struct TileGeo {
     int nx, ny;
     const LogTables *tbl;
     float rho_ref[4];
+    unsigned long long l2_pol = 0;  // L2 policy of the population loads (EF steps)
 };
 
 // The default hook of step_tile_pair: nothing before the first barrier.
@@ -939,8 +957,9 @@ struct NoHook {
 // both components.  Same arithmetic as the general step_tile below, bitwise.
 // The densities phase reads only `geo`; `hook` runs on every thread at its end, before the
 // first barrier, after which P is read (the batched kernel completes its parameter block
-// in shared memory there).
-template <int LAT, int NP, int TX, int TY, int FORCE, int MU, int LD = 0, class Hook = NoHook>
+// in shared memory there).  EF (one pair, L2-only loads): the population loads carry the
+// evict-first policy geo.l2_pol.
+template <int LAT, int NP, int TX, int TY, int FORCE, int MU, int LD = 0, class Hook = NoHook, bool EF = false>
 __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, float *__restrict__ fout,
                                                const DevParams &P, int x0, int y0, const TileGeo geo,
                                                const Hook &hook) {
@@ -979,8 +998,10 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
     // pointers would spill at their 64 registers).
     const unsigned pl = (unsigned)plane;
     // element e of plane i of component c, from the node offset o of plane 0
+    static_assert(!EF || (NP == 1 && LD == 1), "evict-first loads: one pair, L2-only loads");
     auto ld = [&](int c, int i, unsigned o) -> float {
-        if constexpr (NP == 1) return ld_pop<LD>(&(fin + c * cq)[i * pl + o]);
+        if constexpr (EF) return ld_pop_policy(&(fin + c * cq)[i * pl + o], geo.l2_pol);
+        else if constexpr (NP == 1) return ld_pop<LD>(&(fin + c * cq)[i * pl + o]);
         else return ld_pop<LD>(&fin[(size_t)c * cq + (size_t)i * plane + o]);
     };
     // ---- phase 1a: own node -> shared (populations, densities) ------------------
@@ -1145,12 +1166,14 @@ __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, fl
 }
 
 // The lane-pair step with its geometry from the parameter block.
-template <int LAT, int NP, int TX, int TY, int FORCE, int MU, int LD = 0>
+template <int LAT, int NP, int TX, int TY, int FORCE, int MU, int LD = 0, bool EF = false>
 __device__ __forceinline__ void step_tile_pair(const float *__restrict__ fin, float *__restrict__ fout,
                                                const DevParams &P, int x0, int y0) {
-    step_tile_pair<LAT, NP, TX, TY, FORCE, MU, LD>(
+    step_tile_pair<LAT, NP, TX, TY, FORCE, MU, LD, NoHook, EF>(
         fin, fout, P, x0, y0,
-        TileGeo{P.nx, P.ny, P.tbl, {P.rho_ref_f[0], P.rho_ref_f[1], P.rho_ref_f[2], P.rho_ref_f[3]}}, NoHook());
+        TileGeo{P.nx, P.ny, P.tbl, {P.rho_ref_f[0], P.rho_ref_f[1], P.rho_ref_f[2], P.rho_ref_f[3]},
+                EF ? l2_evict_first_policy() : 0ull},
+        NoHook());
 }
 
 // The fused step on one TX x TY tile with origin (x0, y0) of the lattice described by P.

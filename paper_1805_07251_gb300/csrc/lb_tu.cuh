@@ -121,6 +121,15 @@ cudaError_t LBVDW_CAT(LBVDW_NAME, _chain)(const StepLaunch &a, const ChainArgs &
     cfg.numAttrs = pdl ? 1 : 0;
     const float *fin = static_cast<const float *>(a.fin);
     float *fout = static_cast<float *>(a.fout);
+    if (ca.evict_first) {
+        switch (a.force) {
+            case 0: return cudaLaunchKernelEx(&cfg, lb_chain_kernel<0, MUV, true>, fin, fout, a.P, ca);
+            case 1: return cudaLaunchKernelEx(&cfg, lb_chain_kernel<1, MUV, true>, fin, fout, a.P, ca);
+            case 2: return cudaLaunchKernelEx(&cfg, lb_chain_kernel<2, MUV, true>, fin, fout, a.P, ca);
+            case 3: return cudaLaunchKernelEx(&cfg, lb_chain_kernel<3, MUV, true>, fin, fout, a.P, ca);
+        }
+        return cudaErrorInvalidConfiguration;
+    }
     switch (a.force) {
         case 0: return cudaLaunchKernelEx(&cfg, lb_chain_kernel<0, MUV>, fin, fout, a.P, ca);
         case 1: return cudaLaunchKernelEx(&cfg, lb_chain_kernel<1, MUV>, fin, fout, a.P, ca);

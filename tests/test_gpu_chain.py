@@ -4,7 +4,8 @@ completion flags of the 3 x 3 tiles around them.  The arithmetic of a tile is un
 so n chained steps must be bitwise equal to n single-step calls (one plain launch each):
 on lattices of many tile rows (flags on the first rows only), of fewer rows than one wave
 (every row sets flags), with ragged tiles, with the "nid" force, the moment-space
-collision, FP32 mu, and chains cut by check_every."""
+collision, FP32 mu, and chains cut by check_every; with the evict-first L2 policy of the
+input (every lattice of the first test) and without it (4096^2 in the long-chain test)."""
 import numpy as np
 import pytest
 
@@ -155,6 +156,26 @@ def test_steps_captured_in_a_cuda_graph_replay_like_single_steps(gpu_lib):
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("n,evict_first", [(1024, True), (1536, False), (4096, False)])
+def test_l2_policy_of_the_chain_follows_the_buffer_size(gpu_lib, n, evict_first):
+    # the chained steps mark their input evict-first in the L2 where one population buffer
+    # (72 B per node for two FP32 components) takes at most 60 % of the L2: 75.5 MB at
+    # 1024^2 (of GB300's ~126 MB), not 170 MB at 1536^2; single steps never do
+    from paper_1805_07251_gb300 import Simulation
+
+    p = lbinputs.base_params("c2")
+    s = Simulation(precision="fp32_dfmu", device=0, **lbinputs.lib_kwargs(p, nx=n, ny=n))
+    try:
+        assert s.chain_rows > 0 and s.chain_evict_first == evict_first
+    finally:
+        s.close()
+    s = Simulation(precision="fp64", device=0, **lbinputs.lib_kwargs(p, nx=256, ny=256))
+    try:
+        assert s.chain_rows == 0 and not s.chain_evict_first
+    finally:
+        s.close()
 
 
 @pytest.mark.parametrize("n,steps", [(1024, 3000), (4096, 120)])
