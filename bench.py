@@ -90,7 +90,7 @@ TRAFFIC = {"fp32_dfmu": {"digest": "7beb09f974cde77630c9b30434b768a5bf723b374759
                          "profile": "profiles/lb_chain_kernel_fp32_dfmu_c2_1024.md"}}
 # FP64-pipe utilisation of the two FP64-bound paths (sm__pipe_fp64_cycles_active of one
 # launch, the profile named beside it), valid for the kernel sources of the same digest
-FP64_PIPE = {"digest": "86ef663985505818c509fa6d3f43d9dcc73efe8364c65302f1517af9a47ee3d1",
+FP64_PIPE = {"digest": "7beb09f974cde77630c9b30434b768a5bf723b374759841067535a37725fe51c",
              "fp32_mixed": 0.840, "fp64": 0.851, "profile": "profiles/lb_step_kernel_fp64_c2_1024.md"}
 # nominal HBM3e bandwidth of the GPU (GB/s), reported beside the measured copy peak
 HBM_NOMINAL_GBS = 7900.0
